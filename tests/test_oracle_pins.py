@@ -1,0 +1,555 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself.
+
+Each test cites the passage of Mang & Biros (arXiv:1408.6299) it follows and
+checks the oracle against one of: a brute-force O(N^2) DFT, numpy's FFT (an
+independent transform), closed forms of the discrete scheme, dense-matrix
+brute force of the whole discrete method on tiny grids, exact identities of
+the discretisation (skew-adjointness, adjoint transport, mass conservation,
+Gauss-Newton energy identity), finite differences, and values printed in the
+paper (Tab. 5.2 eigenvalue maxima, tests/golden/).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1408_6299_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def hd(n):
+    return float(np.prod([2 * np.pi / k for k in n]))
+
+
+# ---------------------------------------------------------------------------
+# P1 FFT (Sec. 3.3.1 "Fourier spectral methods"): brute-force DFT, inverse, Parseval
+# ---------------------------------------------------------------------------
+
+def brute_dft(a, inverse=False):
+    out = a.astype(np.complex128)
+    sign = 1.0 if inverse else -1.0
+    for ax, n in enumerate(a.shape):
+        j = np.arange(n)
+        W = np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+        out = np.moveaxis(np.tensordot(W, np.moveaxis(out, ax, 0), axes=(1, 0)), 0, ax)
+        if inverse:
+            out = out / n
+    return out
+
+
+@pytest.mark.parametrize("shape", [(2,), (8,), (32,), (8, 8), (4, 16), (4, 4, 4), (2, 8, 4)])
+def test_fft_matches_bruteforce_dft(shape):
+    r = rng(sum(shape))
+    a = r.standard_normal(shape) + 1j * r.standard_normal(shape)
+    F = O.fft(a)
+    ref = brute_dft(a)
+    assert np.abs(F - ref).max() <= 1e-13 * np.abs(ref).max()
+    back = O.fft(F, inverse=True)
+    assert np.abs(back - a).max() <= 1e-14 * np.abs(a).max() * 10
+    assert np.abs(O.fft(a, inverse=True) - brute_dft(a, inverse=True)).max() <= 1e-13 * np.abs(a).max()
+    # Parseval: sum |a|^2 = (1/N) sum |F|^2
+    N = a.size
+    assert abs((np.abs(a) ** 2).sum() - (np.abs(F) ** 2).sum() / N) <= 1e-12 * (np.abs(a) ** 2).sum()
+
+
+def test_fft_larger_against_numpy():
+    a = rng(3).standard_normal((16, 32, 8)) + 0j
+    assert np.abs(O.fft(a) - np.fft.fftn(a)).max() <= 1e-12 * np.abs(np.fft.fftn(a)).max()
+
+
+# ---------------------------------------------------------------------------
+# P2 spectral derivatives, A and K on trigonometric polynomials (Sec. 3.3.1,
+# Eq. first-variation-H1/H2, Eq. eliminated-control)
+# ---------------------------------------------------------------------------
+
+def test_gradient_of_sin2_template_is_exact():
+    n = (32, 32)
+    P = O.Problem(n, 4)
+    X = synth.coords(n)
+    u = 0.5 * (np.sin(X[0]) ** 2 + np.sin(X[1]) ** 2)
+    g = P.grad(u)
+    assert np.abs(g[0] - 0.5 * np.sin(2 * X[0])).max() < 1e-13
+    assert np.abs(g[1] - 0.5 * np.sin(2 * X[1])).max() < 1e-13
+
+
+def test_gradient_divergence_3d_trig():
+    n = (8, 16, 8)
+    P = O.Problem(n, 4)
+    X = synth.coords(n)
+    u = np.sin(2 * X[0] + X[1]) * np.cos(3 * X[2]) + np.cos(X[1] - X[0])
+    g = P.grad(u)
+    ex = [2 * np.cos(2 * X[0] + X[1]) * np.cos(3 * X[2]) + np.sin(X[1] - X[0]),
+          np.cos(2 * X[0] + X[1]) * np.cos(3 * X[2]) - np.sin(X[1] - X[0]),
+          -3 * np.sin(2 * X[0] + X[1]) * np.sin(3 * X[2])]
+    for i in range(3):
+        assert np.abs(g[i] - ex[i]).max() < 1e-13
+    w = np.stack([np.sin(X[1]), np.cos(X[0] + X[2]), np.sin(2 * X[2])])
+    assert np.abs(P.div(w) - 2 * np.cos(2 * X[2])).max() < 1e-13
+
+
+def test_nyquist_reading():
+    """Reading R1: first derivatives drop the Nyquist mode; a(k) keeps it."""
+    n = (16, 8)
+    X = synth.coords(n)
+    u = np.cos(8 * X[0])  # pure Nyquist mode on axis 0
+    for reg in (1, 2):
+        P = O.Problem(n, 4, reg=reg)
+        assert np.abs(P.grad(u)).max() < 1e-14
+        assert np.abs(P.apply_A(u) - (64.0 ** reg) * u).max() < 1e-9 * 64.0 ** reg
+
+
+@pytest.mark.parametrize("reg", [1, 2])
+def test_apply_A_symbol(reg):
+    n = (16, 16, 16)
+    P = O.Problem(n, 4, reg=reg)
+    X = synth.coords(n)
+    u = np.cos(3 * X[0] - 2 * X[1] + 5 * X[2]) + 2.0
+    kk = 9 + 4 + 25
+    assert np.abs(P.apply_A(u) - kk ** reg * (u - 2.0)).max() < 1e-10 * kk ** reg
+
+
+def test_leray_on_gradient_and_solenoidal_fields():
+    n = (16, 16)
+    P = O.Problem(n, 4)
+    X = synth.coords(n)
+    phi = np.sin(2 * X[0]) * np.cos(X[1])
+    gphi = P.grad(phi)
+    assert np.abs(P.leray(gphi)).max() < 1e-13
+    psi = np.cos(X[0] + 3 * X[1])
+    sol = np.stack([-3 * np.sin(X[0] + 3 * X[1]), np.sin(X[0] + 3 * X[1])])  # curl of psi: div = 0
+    assert np.abs(P.leray(sol) - sol).max() < 1e-13
+    const = np.ones((2,) + n)
+    assert np.abs(P.leray(const) - const).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# P3 skew/self-adjointness, projector identities
+# ---------------------------------------------------------------------------
+
+def test_skew_and_projector_identities():
+    n = (8, 16, 8)
+    P = O.Problem(n, 4)
+    r = rng(5)
+    a, b = r.standard_normal(n), r.standard_normal(n)
+    ga, gb = P.grad(a), P.grad(b)
+    for i in range(3):
+        assert abs((ga[i] * b).sum() + (a * gb[i]).sum()) < 1e-12 * np.abs(ga[i] * b).sum()
+    w, z = r.standard_normal((3,) + n), r.standard_normal((3,) + n)
+    Kw, Kz = P.leray(w), P.leray(z)
+    assert abs((Kw * z).sum() - (w * Kz).sum()) < 1e-12 * np.abs(w * z).sum()
+    assert np.abs(P.leray(Kw) - Kw).max() < 1e-13 * np.abs(Kw).max()
+    assert np.abs(P.div(Kw)).max() < 1e-12 * np.abs(w).max()
+    Aa = P.apply_A(a)
+    assert abs((Aa * b).sum() - (a * P.apply_A(b)).sum()) < 1e-12 * np.abs(Aa * b).sum()
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev basis and Gram matrix (Sec. 3.3.2, App. A; reading R3)
+# ---------------------------------------------------------------------------
+
+def test_chebyshev_basis_and_gram():
+    from numpy.polynomial import chebyshev as C
+    for nc in (1, 2, 5):
+        for t in (0.0, 0.3, 1.0):
+            ref = [C.chebval(2 * t - 1, [0] * l + [1]) for l in range(nc)]
+            assert np.allclose(O.cheb_eval(nc, t), ref, atol=1e-15)
+        x, w = np.polynomial.legendre.leggauss(40)
+        t = 0.5 * (x + 1)
+        B = np.stack([C.chebval(2 * t - 1, [0] * l + [1]) for l in range(nc)])
+        ref = 0.5 * (B * w) @ B.T
+        assert np.abs(O.cheb_gram(nc) - ref).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# P4 preconditioner (Sec. 3.3.3; Sec. 3.2.1 left preconditioner beta A)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nc,reg", [(1, 1), (1, 2), (3, 1)])
+def test_preconditioner_inverts_regularisation(nc, reg):
+    n = (16, 8)
+    P = O.Problem(n, 4, n_c=nc, beta=3e-3, reg=reg)
+    r = rng(7)
+    u = r.standard_normal(P.coef_shape())
+    u -= u.mean(axis=(2, 3), keepdims=True)
+    back = P.precond(P.reg_apply(u))
+    assert np.abs(back - u).max() < 1e-12 * np.abs(u).max()
+    # k = 0 mode: identity (times C^-1 across coefficients)
+    c = np.ones(P.coef_shape()) * r.standard_normal((nc, 2, 1, 1))
+    Cinv = np.linalg.inv(O.cheb_gram(nc))
+    assert np.abs(P.precond(c) - np.einsum("lm,mi...->li...", Cinv, c)).max() < 1e-13
+
+
+def test_reg_apply_against_numpy():
+    n = (16, 16)
+    P = O.Problem(n, 4, n_c=2, beta=0.7, reg=2)
+    r = rng(8)
+    v = r.standard_normal(P.coef_shape())
+    k = np.fft.fftfreq(16, 1 / 16)
+    k[8] = -8
+    K = np.meshgrid(k, k, indexing="ij")
+    a = (K[0] ** 2 + K[1] ** 2) ** 2
+    Av = np.real(np.fft.ifftn(a * np.fft.fftn(v, axes=(2, 3)), axes=(2, 3)))
+    ref = 0.7 * np.einsum("lm,mi...->li...", O.cheb_gram(2), Av)
+    assert np.abs(P.reg_apply(v) - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# P5 constant velocity: closed form of the Heun scheme (Sec. 3.3.1)
+# ---------------------------------------------------------------------------
+
+def test_constant_velocity_closed_form():
+    n = (16, 8)
+    nt = 8
+    P = O.Problem(n, nt)
+    c = np.array([0.37, -0.8])
+    v = np.ones((1, 2) + n) * c[None, :, None, None]
+    m0 = rng(9).standard_normal(n)
+    mt = P.state(v, m0)
+    k = [np.fft.fftfreq(m, 1 / m) for m in n]
+    for i, m in enumerate(n):
+        k[i][m // 2] = 0.0  # masked first-derivative wavenumber
+    K = np.meshgrid(*k, indexing="ij")
+    z = (1.0 / nt) * (-1j) * (c[0] * K[0] + c[1] * K[1])
+    R = 1 + z + z * z / 2
+    ref = np.real(np.fft.ifftn(R ** nt * np.fft.fftn(m0)))
+    assert np.abs(mt[-1] - ref).max() < 1e-13 * np.abs(m0).max() * 10
+    det = P.detF(v)
+    assert np.abs(det - 1).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# P6 mass conservation (div-free v) and adjoint mass conservation (any v)
+# ---------------------------------------------------------------------------
+
+def test_mass_conservation():
+    c = synth.stokes_3d(16, n_t=8, n_c=2)
+    P = O.Problem(c["n"], 8, n_c=2)
+    mt = P.state(c["v_true"], c["mT"])
+    s0 = c["mT"].sum()
+    assert np.abs(mt.reshape(9, -1).sum(axis=1) - s0).max() < 1e-12 * np.abs(c["mT"]).sum()
+    v = rng(10).standard_normal(P.coef_shape()) * 0.1  # not divergence-free
+    lam = P.adjoint(v, c["mT"])
+    assert np.abs(lam.reshape(9, -1).sum(axis=1) - s0).max() < 1e-12 * np.abs(c["mT"]).sum()
+
+
+# ---------------------------------------------------------------------------
+# P7 exact discrete transport adjoint: <Phi m0, w> = <m0, Phi^T w> (Eq.
+# first-order-forward / first-order-adjoint; one Heun step transposes into the
+# backward Heun step because L^T = D)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nc", [1, 3])
+def test_transport_adjoint_identity(nc):
+    n = (8, 16)
+    P = O.Problem(n, 6, n_c=nc)
+    r = rng(11 + nc)
+    v = 0.3 * r.standard_normal(P.coef_shape())
+    m0, w = r.standard_normal(n), r.standard_normal(n)
+    lhs = (P.state(v, m0)[-1] * w).sum()
+    rhs = (m0 * P.adjoint(v, w)[0]).sum()
+    assert abs(lhs - rhs) < 1e-13 * (abs(lhs) + np.abs(m0 * w).sum())
+
+
+# ---------------------------------------------------------------------------
+# P8 zero velocity closed forms (Eq. first-order-control, Eq. gauss-newton)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("stokes", [False, True])
+def test_zero_velocity_gradient_and_hessian(stokes):
+    n = (16, 16)
+    X = synth.coords(n)
+    mT = 0.5 * (np.sin(X[0]) ** 2 + np.sin(X[1]) ** 2)
+    gmT = np.stack([0.5 * np.sin(2 * X[0]), 0.5 * np.sin(2 * X[1])])
+    mR = np.cos(X[0] + X[1]) * 0.3 + mT
+    P = O.Problem(n, 4, beta=0.05, reg=1, stokes=stokes)
+    v0 = np.zeros(P.coef_shape())
+    g, J = P.gradient(v0, mT, mR)
+    f = (mR - mT) * gmT
+    if stokes:  # independent Leray projection via numpy
+        k = np.fft.fftfreq(16, 1 / 16)
+        k[8] = 0
+        K = np.meshgrid(k, k, indexing="ij")
+        kk = K[0] ** 2 + K[1] ** 2
+        kk[kk == 0] = 1.0  # numerator vanishes there too: identity on those modes
+        F = np.fft.fftn(f, axes=(1, 2))
+        dotk = K[0] * F[0] + K[1] * F[1]
+        f = np.real(np.fft.ifftn(np.stack([F[0] - K[0] * dotk / kk, F[1] - K[1] * dotk / kk]), axes=(1, 2)))
+    assert np.abs(g[0] - f).max() < 1e-13
+    assert abs(J - 0.5 * hd(n) * ((mR - mT) ** 2).sum()) < 1e-13 * J
+    vt = np.stack([np.cos(X[1]), np.sin(2 * X[0] + X[1])])[None]
+    H = P.hessvec(v0, mT, vt)
+    s = (gmT * vt[0]).sum(axis=0)
+    data = s * gmT
+    if stokes:
+        F = np.fft.fftn(data, axes=(1, 2))
+        dotk = K[0] * F[0] + K[1] * F[1]
+        data = np.real(np.fft.ifftn(np.stack([F[0] - K[0] * dotk / kk, F[1] - K[1] * dotk / kk]), axes=(1, 2)))
+    reg = 0.05 * np.stack([vt[0, 0] * 1.0, vt[0, 1] * 5.0])  # |k|^2 of each component
+    assert np.abs(H[0] - (reg + data)).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# P9 printed eigenvalue maxima at beta = 1e6 (Tab. 5.2)
+# ---------------------------------------------------------------------------
+
+def test_beta_1e6_eigenvalue_maxima_match_paper():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "eigen_beta1e6_64.txt")) if not ln.startswith("#")]
+    c = synth.blobs_2d(64, n_t=8)
+    for reg_name, stokes, value, digits in rows:
+        reg = 1 if reg_name == "H1" else 2
+        P = O.Problem((64, 64), 8, beta=1e6, reg=reg, stokes=bool(int(stokes)))
+        j = np.arange(64)
+        e = np.zeros(P.coef_shape())
+        e[0, 0] = np.outer((-1.0) ** j, (-1.0) ** j)  # Nyquist corner mode, the top of a(k)
+        x = e
+        for _ in range(3):  # a few power steps from the corner mode
+            Hx = P.hessvec(c["v_true"], c["mT"], x)
+            lam = (x * Hx).sum() / (x * x).sum()
+            x = Hx / np.abs(Hx).max()
+        assert float(f"{lam:.{int(digits) - 1}e}") == float(value)
+
+
+# ---------------------------------------------------------------------------
+# Dense brute force of the whole discrete method on a tiny grid (Sec. 3.3.1,
+# Alg. 1-2, Eq. gauss-newton, App. A): every operator is an explicit matrix
+# built from numpy's FFT, the Heun steps are matrix products.
+# ---------------------------------------------------------------------------
+
+class Dense:
+    def __init__(self, n, nt, nc, beta, reg, stokes):
+        self.n, self.nt, self.nc, self.beta = n, nt, nc, beta
+        N = int(np.prod(n))
+        self.N, self.d = N, len(n)
+        I = np.eye(N).reshape((N,) + n)
+        axes = tuple(range(1, self.d + 1))
+        FI = np.fft.fftn(I, axes=axes)
+        ks = []
+        for i, m in enumerate(n):
+            k = np.fft.fftfreq(m, 1 / m)
+            k[m // 2] = -m // 2
+            ks.append(k)
+        Kf = np.meshgrid(*ks, indexing="ij")
+        Km = [np.where(np.abs(k) == m // 2, 0.0, k) for k, m in zip(Kf, n)]
+        def op(sym):
+            return np.real(np.fft.ifftn(FI * sym[None], axes=axes)).reshape(N, N).T
+        self.D = [op(1j * Km[i]) for i in range(self.d)]
+        a = sum(k ** 2 for k in Kf) ** reg
+        self.A = op(a)
+        kk = sum(k ** 2 for k in Km)
+        kk1 = np.where(kk == 0, 1.0, kk)
+        self.K = None
+        if stokes:
+            blocks = [[op((1.0 if i == j else 0.0) - np.where(kk == 0, 0.0, Km[i] * Km[j] / kk1)) for j in range(self.d)]
+                      for i in range(self.d)]
+            self.K = np.block(blocks)
+        self.C = O.cheb_gram(nc)
+        self.h = 1.0 / nt
+
+    def b(self, t):
+        from numpy.polynomial import chebyshev as C
+        return np.array([C.chebval(2 * t - 1, [0] * l + [1]) for l in range(self.nc)])
+
+    def vel(self, v, t):
+        return np.einsum("l,lix->ix", self.b(t), v.reshape(self.nc, self.d, self.N))
+
+    def L(self, v, t):
+        vt = self.vel(v, t)
+        return -sum(vt[i][:, None] * self.D[i] for i in range(self.d))
+
+    def state(self, v, m0):
+        ms = [m0.reshape(-1)]
+        h = self.h
+        for j in range(self.nt):
+            La, Lb = self.L(v, j * h), self.L(v, (j + 1) * h)
+            step = np.eye(self.N) + h / 2 * (La + Lb) + h * h / 2 * Lb @ La
+            ms.append(step @ ms[-1])
+        return ms
+
+    def adjoint(self, v, lend):
+        h = self.h
+        ls = [None] * (self.nt + 1)
+        ls[-1] = lend
+        for j in range(self.nt - 1, -1, -1):
+            La, Lb = self.L(v, j * h), self.L(v, (j + 1) * h)
+            step = np.eye(self.N) + h / 2 * (La + Lb) + h * h / 2 * Lb @ La
+            ls[j] = step.T @ ls[j + 1]
+        return ls
+
+    def force(self, ms, ls):
+        h = self.h
+        f = np.zeros((self.nc, self.d, self.N))
+        for j in range(self.nt + 1):
+            w = h / 2 if j in (0, self.nt) else h
+            gm = np.stack([D @ ms[j] for D in self.D])
+            f += w * self.b(j * h)[:, None, None] * (ls[j] * gm)[None]
+        return f
+
+    def tail(self, v, f):
+        v = v.reshape(self.nc, self.d, self.N)
+        out = self.beta * np.einsum("lm,mix->lix", self.C, np.einsum("xy,miy->mix", self.A, v))
+        for l in range(self.nc):
+            out[l] += (self.K @ f[l].reshape(-1)).reshape(self.d, self.N) if self.K is not None else f[l]
+        return out
+
+    def hessvec(self, v, mT, vt):
+        ms = self.state(v, mT)
+        h = self.h
+        y = np.zeros(self.N)
+        for j in range(self.nt):
+            La, Lb = self.L(v, j * h), self.L(v, (j + 1) * h)
+            sa = -(np.stack([D @ ms[j] for D in self.D]) * self.vel(vt, j * h)).sum(0)
+            sb = -(np.stack([D @ ms[j + 1] for D in self.D]) * self.vel(vt, (j + 1) * h)).sum(0)
+            k1 = La @ y + sa
+            k2 = Lb @ (y + h * k1) + sb
+            y = y + h / 2 * (k1 + k2)
+        ls = self.adjoint(v, -y)
+        return self.tail(vt, self.force(ms, ls))
+
+    def gradient(self, v, mT, mR):
+        ms = self.state(v, mT)
+        ls = self.adjoint(v, mR.reshape(-1) - ms[-1])
+        return self.tail(v, self.force(ms, ls))
+
+
+@pytest.mark.parametrize("nc,reg,stokes", [(1, 1, False), (2, 2, False), (2, 1, True)])
+def test_whole_method_matches_dense_brute_force(nc, reg, stokes):
+    n = (8, 4)
+    nt = 3
+    r = rng(20 + nc + reg)
+    v = 0.4 * r.standard_normal((nc, 2) + n)
+    vt = r.standard_normal((nc, 2) + n)
+    X = synth.coords(n)
+    mT = np.sin(X[0]) * np.cos(X[1]) + 0.2 * r.standard_normal(n)
+    mR = r.standard_normal(n)
+    P = O.Problem(n, nt, n_c=nc, beta=0.03, reg=reg, stokes=stokes)
+    Dn = Dense(n, nt, nc, 0.03, reg, stokes)
+    H = P.hessvec(v, mT, vt).reshape(nc, 2, -1)
+    Hd = Dn.hessvec(v, mT, vt)
+    assert np.abs(H - Hd).max() < 1e-12 * np.abs(Hd).max()
+    g, J = P.gradient(v, mT, mR)
+    gd = Dn.gradient(v, mT, mR)
+    assert np.abs(g.reshape(nc, 2, -1) - gd).max() < 1e-12 * np.abs(gd).max()
+    m1 = Dn.state(v, mT)[-1]
+    vv = v.reshape(nc, 2, -1)
+    reg_term = 0.03 * np.einsum("lm,lix,xy,miy->", O.cheb_gram(nc), vv, Dn.A, vv)
+    Jd = 0.5 * hd(n) * (((mR.reshape(-1) - m1) ** 2).sum() + reg_term)
+    assert abs(J - Jd) < 1e-12 * Jd
+    assert abs(P.objective(v, mT, mR)[0] - Jd) < 1e-12 * Jd
+
+
+# ---------------------------------------------------------------------------
+# P10-P12 discrete-adjoint (test-only) variant: energy identity, FD of J,
+# Hessian symmetry and the inverse-crime Newton limit; trapezoid variant
+# converges to it at second order (reading R4).
+# ---------------------------------------------------------------------------
+
+def small_problem(nt=8, nc=2, stokes=False, dto=True, reg=1):
+    n = (16, 16)
+    r = rng(30)
+    X = synth.coords(n)
+    mT = 0.5 * (np.sin(X[0]) ** 2 + np.sin(X[1]) ** 2) + 0.05 * synth.random_spectral_field(n, r, 4.0)
+    v = np.stack([synth.velocity_field(n, r, 4, 0.3, divergence_free=stokes) for _ in range(nc)])
+    P = O.Problem(n, nt, n_c=nc, beta=1e-2, reg=reg, stokes=stokes, dto=dto)
+    return P, mT, v, r
+
+
+def test_gn_energy_identity_dto():
+    P, mT, v, r = small_problem()
+    vt = np.stack([synth.velocity_field(P.n, r, 6, 1.0) for _ in range(2)])
+    H = P.hessvec(v, mT, vt)
+    data = H - P.reg_apply(vt)
+    eps = 1e-5
+    mp = P.state(v + eps * vt, mT)[-1]
+    mm = P.state(v - eps * vt, mT)[-1]
+    dm = (mp - mm) / (2 * eps)
+    lhs = P.hd * (vt * data).sum()
+    rhs = P.hd * (dm ** 2).sum()
+    assert abs(lhs - rhs) < 1e-8 * rhs
+
+
+def test_gradient_matches_finite_differences_dto():
+    P, mT, v, r = small_problem()
+    mR = P.state(v * 1.3, mT)[-1] + 0.01 * synth.random_spectral_field(P.n, r, 5.0)
+    g, J = P.gradient(v, mT, mR)
+    eps = 1e-6
+    for s in range(5):
+        w = rng(100 + s).standard_normal(P.coef_shape())
+        fd = (P.objective(v + eps * w, mT, mR)[0] - P.objective(v - eps * w, mT, mR)[0]) / (2 * eps)
+        an = P.hd * (g * w).sum()
+        assert abs(fd - an) < 1e-7 * abs(an) + 1e-10
+
+
+def test_hessian_symmetry_dto_and_inverse_crime_newton_limit():
+    P, mT, v, r = small_problem(stokes=False)
+    a = rng(40).standard_normal(P.coef_shape())
+    b = rng(41).standard_normal(P.coef_shape())
+    Ha, Hb = P.hessvec(v, mT, a), P.hessvec(v, mT, b)
+    assert abs((b * Ha).sum() - (a * Hb).sum()) < 1e-12 * abs((b * Ha).sum())
+    mR = P.state(v, mT)[-1]  # inverse crime: lambda = 0, GN equals Newton
+    eps = 1e-5
+    gp = P.gradient(v + eps * a, mT, mR)[0]
+    gm = P.gradient(v - eps * a, mT, mR)[0]
+    assert np.abs((gp - gm) / (2 * eps) - Ha).max() < 1e-7 * np.abs(Ha).max()
+
+
+def test_trapezoid_converges_to_discrete_adjoint_at_second_order():
+    errs = []
+    for nt in (8, 16, 32):
+        Pd, mT, v, r = small_problem(nt=nt, dto=True)
+        Pt, _, _, _ = small_problem(nt=nt, dto=False)
+        vt = rng(50).standard_normal(Pd.coef_shape())
+        Hd, Ht = Pd.hessvec(v, mT, vt), Pt.hessvec(v, mT, vt)
+        errs.append(np.linalg.norm(Hd - Ht) / np.linalg.norm(Hd))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# P13 second order in time of the state solve (Sec. 1.2: second order in time)
+# ---------------------------------------------------------------------------
+
+def test_state_second_order_in_time():
+    c = synth.sinusoid_2d()
+    ref = O.Problem(c["n"], 512).state(c["v_true"], c["mT"])[-1]
+    errs = [np.abs(O.Problem(c["n"], nt).state(c["v_true"], c["mT"])[-1] - ref).max() for nt in (16, 32, 64)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 2) < 0.15), (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# P14 det F for a divergence-free velocity (App. D Eq. def-grad): det F_1 -> 1
+# at second order in h_t
+# ---------------------------------------------------------------------------
+
+def test_detF_divergence_free_second_order():
+    n = (32, 32)
+    X = synth.coords(n)
+    vstar = 0.5 * np.stack([np.sin(X[1]) * np.cos(X[0]), -np.sin(X[0]) * np.cos(X[1])])[None]
+    errs = [np.abs(O.Problem(n, nt).detF(vstar) - 1).max() for nt in (16, 32, 64, 128)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+    assert errs[-1] < 3e-6
+
+
+# ---------------------------------------------------------------------------
+# Solve (Alg. 1 with Eq. termination-criterion-ksm and Armijo line search):
+# the smooth 32^2 workload converges in a handful of Gauss-Newton steps
+# without backtracking, as Tab. 5.3 reports for the smooth problem.
+# ---------------------------------------------------------------------------
+
+def test_solve_smooth_problem():
+    c = synth.sinusoid_2d()
+    P = O.Problem(c["n"], c["n_t"], beta=c["beta"], reg=c["reg"])
+    mR = P.state(c["v_true"], c["mT"])[-1]
+    v, rep = P.solve(c["mT"], mR, grad_rtol=1e-2)
+    assert rep["status"] == 0
+    assert rep["g_inf"] <= 1e-2 * rep["g0_inf"]
+    assert 2 <= rep["outer"] <= 8
+    assert rep["ls_trials"] == rep["outer"]  # alpha = 1 accepted every time
+    assert rep["J"] < 0.5 * rep["J0"]
