@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Gauss-Newton Hessian matvecs/s on the 256^3 random-field registration workload.
+
+Workload (one step = one Hessian matvec, Alg. 2 of Mang & Biros): 256^3 grid,
+H2 regularisation, beta = 1e-3, stationary velocity (n_c = 1), n_t = 64 Heun
+steps, state checkpoints every 8 steps recomputed in both sweeps, single
+precision transport sweeps with double precision outer vectors (REG_MIXED).
+Inputs are seeded synthetic fields (paper_1408_6299_gb300.synth.random_3d):
+a unit-variance template band-limited to |k| <= 48, a smooth velocity of max
+speed 0.5 (|k| <= 8) and a unit-speed direction. Every field is 64-128 MB,
+well above the 129 MB L2 in aggregate per step (the state checkpoints alone
+are 580 MB), so no explicit L2 flush is done.
+
+One process per GPU (torchrun); with several GPUs every rank runs its own
+replica of the workload (the solver does not shard) and value counts the
+matvecs of all ranks over the slowest rank's time.
+
+--impl reference times the CPU oracle (oracle/) on the same workload: each
+step is one oracle matvec on the 256^3 grid with n_t = 2, and the n_t = 64
+cost is extrapolated from the n_t = 1 and n_t = 2 runs.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian matvecs/s at 256^3 (FP32-Krylov vs FP64) and solve time to rel-grad 1e-2"
+UNIT = "matvecs/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--n_t", type=int, default=64)
+    p.add_argument("--ckpt", type=int, default=8)
+    p.add_argument("--fp64-steps", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(kind):
+    """Per-launch DRAM bytes of `kind` from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kind)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != ent.get("source_sha256_16"):
+        return None
+    return float(ent["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_matvec_seconds(c, n_t):
+    from oracle import oracle as O
+    P = O.Problem(c["n"], n_t, c["n_c"], c["beta"], c["reg"], c["stokes"])
+    t = time.perf_counter()
+    P.hessvec(c["v_true"], c["mT"], c["vt"])
+    return time.perf_counter() - t
+
+
+def oracle_extrapolated(c, n_t, t1=None, reps=1):
+    """seconds of one full n_t-step oracle matvec from runs with 1 and 2 steps"""
+    if t1 is None:
+        t1 = oracle_matvec_seconds(c, 1)
+    t2s = [oracle_matvec_seconds(c, 2) for _ in range(reps)]
+    t2 = statistics.median(t2s)
+    per_step = max(t2 - t1, 1e-9)
+    return t1 + (n_t - 1) * per_step, t1, t2s
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1408_6299_gb300 import synth
+    c = synth.random_3d(args.n, n_t=args.n_t)
+    t1 = oracle_matvec_seconds(c, 1)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_matvec_seconds(c, 2)
+    T, t1, t2s = oracle_extrapolated(c, args.n_t, t1=t1, reps=args.steps)
+    value = 1.0 / T
+    cores = O.num_threads()
+    sample = (f"oracle GN matvec on the {args.n}^3 grid with n_t=1 (once) and n_t=2 ({args.steps} timed steps); "
+              f"n_t={args.n_t} cost = t1 + {args.n_t - 1}*(t2 - t1)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * T, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"random-field {args.n}^3 H2 beta=1e-3 n_c=1 n_t={args.n_t} GN matvec (CPU oracle)",
+                   "grid": [args.n] * 3, "n_t": args.n_t},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1408_6299_gb300 import lib, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    c = synth.random_3d(args.n, n_t=args.n_t)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    shape = (c["n_c"], 3) + c["n"]
+    R = lib.Registration(c["n"], args.n_t, c["n_c"], c["beta"], c["reg"], c["stokes"], lib.REG_MIXED, args.ckpt)
+    v, mT, vt = dev(c["v_true"]), dev(c["mT"]), dev(c["vt"])
+    mR = torch.empty(c["n"], dtype=torch.float64, device="cuda")
+    R.transport(v, mT, mR)
+    R.set_images(mT, mR)
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    R.gradient(v, g)  # linearisation point of the matvecs (stored state)
+    Hv = torch.empty_like(g)
+    for _ in range(args.warmup):
+        R.hessvec(vt, Hv)
+    # one profiled matvec to find the dominant kernel kind
+    R.profile_begin()
+    R.hessvec(vt, Hv)
+    prof_all = R.profile_end()
+    dominant = max(prof_all, key=lambda k: prof_all[k]["ms"])
+    kind_idx = lib.KIND_NAMES.index(dominant)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = lib.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.profile_begin(1 << kind_idx)
+    e0.record()
+    for _ in range(args.steps):
+        R.hessvec(vt, Hv)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    prof = R.profile_end()[dominant]
+    launches = lib.launch_count() - l0
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    vt_h = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    vt_h.copy_(vt.cpu())
+    Hv_h = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+    R.hessvec(vt_h, Hv_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        R.hessvec(vt_h, Hv_h)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = int(np.prod(shape)) * 8
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    # plain FP64 GPU form (same checkpointing), for the FP32-vs-FP64 comparison
+    fp64 = None
+    if args.fp64_steps > 0:
+        R64 = lib.Registration(c["n"], args.n_t, c["n_c"], c["beta"], c["reg"], c["stokes"], lib.REG_FP64, args.ckpt)
+        R64.set_images(mT, mR)
+        R64.linearize(v)
+        H64 = torch.empty_like(g)
+        R64.hessvec(vt, H64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fp64_steps):
+            R64.hessvec(vt, H64)
+        torch.cuda.synchronize()
+        fp64_s = (time.perf_counter() - t0) / args.fp64_steps
+        mixed_err = float(torch.linalg.vector_norm(Hv - H64) / torch.linalg.vector_norm(H64))
+        fp64 = {"value": 1.0 / fp64_s, "unit": UNIT, "mixed_vs_fp64_rel_err": mixed_err}
+        R64.close()
+
+    peak, peak_src = measured_peaks()
+    achieved = prof["bytes"] / (prof["ms"] / 1000.0) / 1e9 if prof["ms"] > 0 else 0.0
+    traffic = kernel_traffic(dominant)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
+                "peak_source": f"{peak_src} (hbm_gbs)", "launches": prof["launches"],
+                "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
+                "share_of_matvec": prof_all[dominant]["ms"] / max(sum(v["ms"] for v in prof_all.values()), 1e-9)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        T, t1, t2s = oracle_extrapolated(c, args.n_t)
+        cpu = {"value": 1.0 / T, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"oracle GN matvec on the {args.n}^3 grid with n_t=1 ({t1:.1f} s) and n_t=2 "
+                         f"({t2s[0]:.1f} s); n_t={args.n_t} cost extrapolated as t1 + {args.n_t - 1}*(t2 - t1)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"random-field {args.n}^3 H2 beta=1e-3 n_c=1 n_t={args.n_t} GN matvec, "
+                                   f"state checkpoints every {args.ckpt}",
+                       "grid": [args.n] * 3, "n_t": args.n_t, "ckpt_every": args.ckpt,
+                       "precision": "mixed (f32 sweeps, f64 force/tail/vectors)",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "clocks": ck, "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "fp64": fp64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    R.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

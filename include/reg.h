@@ -1,0 +1,217 @@
+/*
+ * reg.h -- C ABI of the GB300 library for the inexact Gauss-Newton-Krylov
+ * diffeomorphic image registration method of Mang & Biros, "An inexact
+ * Newton-Krylov algorithm for constrained diffeomorphic image registration"
+ * (arXiv:1408.6299).
+ *
+ * Problem (Sec. 1.1, Eq. objective / Eq. constraint): find a velocity v(x,t) on
+ * the periodic domain [0,2pi)^d, d in {2,3}, minimising
+ *     J[v] = 1/2 ||m_R - m_1||^2 + beta/2 int_0^1 <B v, B v> dt
+ * subject to dm/dt + grad m . v = 0, m(0) = m_T, and, for the Stokes scheme,
+ * div v = 0. B = grad (H1 seminorm, A = -Lap) or B = Lap (H2, A = Lap^2)
+ * (Sec. 2.1, Eq. first-variation-H1/H2). v is expanded in time in n_c
+ * Chebyshev coefficient fields, v(x,t) = sum_l T_l(2t-1) v_l(x) (Sec. 3.3.2).
+ * Space is discretised by Fourier collocation on the nodal grid
+ * x_j = 2 pi j / n_i, time by Heun's RK2 with h_t = 1/n_t (Sec. 3.3.1).
+ *
+ * Layouts (all row-major, last grid axis fastest, N = n_0*...*n_{d-1}):
+ *   image            double[N]
+ *   coefficient vec  double[n_c][d][N]   (v, v~, gradients, PCG vectors)
+ * Norms and inner products: <u,w>_h = h_d sum_x u.w with h_d = prod 2pi/n_i.
+ *
+ * Pointers: every array argument may be a device pointer (cudaMalloc /
+ * PyTorch CUDA tensor) or a host pointer; the library inspects it with
+ * cudaPointerGetAttributes and stages host arrays through its own device
+ * buffers. The caller owns every array it passes; the library never frees
+ * them and keeps no reference after a call returns (images are copied).
+ * All work is ordered on the context's stream; calls return after that work
+ * has finished (results are valid on return). A context is not thread-safe:
+ * use one context per host thread.
+ *
+ * Errors: every call returns a reg_status; reg_last_error() describes the most
+ * recent failure of that context. No call aborts, traps or exits the process.
+ */
+#ifndef REG_H
+#define REG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define REG_API __attribute__((visibility("default")))
+#else
+#define REG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reg_ctx reg_ctx;
+
+typedef enum {
+  REG_OK = 0,
+  REG_EINVAL = 1,        /* bad argument: grid not a power of two in [8,512], d not 2/3, ... */
+  REG_ENOMEM = 2,        /* device allocation failed */
+  REG_ECUDA = 3,         /* a CUDA runtime call failed */
+  REG_ENOTREADY = 4,     /* reg_hessvec before reg_gradient / reg_linearize */
+  REG_ENONFINITE = 5,    /* objective, gradient or a Krylov scalar is not finite */
+  REG_ECFL = 6,          /* CFL bound could not be met by step halving */
+  REG_ELINESEARCH = 7,   /* Armijo line search exhausted its trials */
+  REG_EMAXIT = 8,        /* outer iteration cap reached before the tolerance */
+  REG_ETIMEOUT = 9       /* a bounded device wait ran out */
+} reg_status;
+
+typedef enum { REG_H1 = 1, REG_H2 = 2 } reg_type;
+
+typedef enum {
+  REG_FP64 = 0,  /* every transport sweep in double precision */
+  REG_MIXED = 1  /* Hessian matvec sweeps in single precision; objective,
+                    gradient, line search, det F and Krylov vectors in double */
+} reg_precision;
+
+typedef enum {
+  REG_QUAD_TRAPEZOID = 0,  /* body-force time integral by the trapezoid rule on
+                              the time nodes (optimize-then-discretize, Sec. 3) */
+  REG_QUAD_DISCRETE = 1    /* exact derivative of the Heun-discretised objective
+                              (stage values; gradient matches finite differences) */
+} reg_quadrature;
+
+/* Create a context (Sec. 3.3: grid n[0..d-1], n_t Heun steps, n_c Chebyshev
+ * coefficients, regularisation weight beta > 0, regulariser type, Stokes flag
+ * gamma, precision of the matvec sweeps, state checkpoint interval
+ * ckpt_every (0 = store the whole state trajectory; K > 0 = keep every K-th
+ * state and recompute the others), and a cudaStream_t (NULL = the legacy
+ * default stream). Requires n_t % ckpt_every == 0 when ckpt_every > 0.
+ * Errors: REG_EINVAL, REG_ENOMEM, REG_ECUDA. On error *out is NULL. */
+REG_API reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, int n_c, double beta, int reg_type,
+                      int stokes, int precision, int ckpt_every, void* cuda_stream);
+
+/* Destroy a context and free its device memory. NULL is accepted. */
+REG_API reg_status reg_destroy(reg_ctx* ctx);
+
+/* Text of the last error of ctx (never NULL; "" when none). Valid until the
+ * next call on ctx. ctx may be NULL (then describes the last failed create). */
+REG_API const char* reg_last_error(const reg_ctx* ctx);
+
+/* Choose the time quadrature of the body force (default trapezoid). */
+REG_API reg_status reg_set_quadrature(reg_ctx* ctx, int quadrature);
+
+/* Copy the template m_T and the reference m_R (N values each) into the
+ * context (Sec. 1.1). Invalidates the linearisation point. */
+REG_API reg_status reg_set_images(reg_ctx* ctx, const double* m_T, const double* m_R);
+
+/* Objective J^h at v (Eq. objective with the expansion of App. A):
+ * one state solve (Eq. first-order-forward) plus the Fourier-diagonal
+ * regularisation term. J_out: host double. parts (may be NULL): host double[2]
+ * = {1/2 ||m_R - m_1||_h^2, beta/2 sum_ll' c_ll' <B v_l, B v_l'>_h}. */
+REG_API reg_status reg_objective(reg_ctx* ctx, const double* v, double* J_out, double* parts);
+
+/* Reduced gradient g at v (Eq. first-order-control with the pressure
+ * eliminated, Eq. eliminated-control, and App. A Eq. control-equation-expansion):
+ * state solve, adjoint solve (Eq. first-order-adjoint, lambda_1 = m_R - m_1),
+ * g_l = beta sum_l' c_ll' A v_l' + int b_l K^gamma[lambda grad m] dt.
+ * Also makes v the linearisation point of later reg_hessvec calls (Alg. 2
+ * takes m_k and v_k as given). g: n_c*d*N doubles. J_out (may be NULL):
+ * host double receiving J at v. Errors: REG_ENONFINITE if J or g is not finite. */
+REG_API reg_status reg_gradient(reg_ctx* ctx, const double* v, double* g, double* J_out);
+
+/* Make v the linearisation point without computing the gradient (one state
+ * solve; the stored state feeds reg_hessvec). */
+REG_API reg_status reg_linearize(reg_ctx* ctx, const double* v);
+
+/* Gauss-Newton reduced-Hessian matvec (Alg. 2 with Eq. gauss-newton and
+ * Eq. eliminated-icontrol): incremental state solve forward from 0,
+ * incremental adjoint solve backward from -m~_1, then
+ * Hvt_l = beta sum_l' c_ll' A vt_l' + int b_l K^gamma[lambda~ grad m] dt,
+ * at the point set by the last reg_gradient / reg_linearize.
+ * vt, Hvt: n_c*d*N doubles (may alias). REG_ENOTREADY without a point. */
+REG_API reg_status reg_hessvec(reg_ctx* ctx, const double* vt, double* Hvt);
+
+/* Preconditioner z = P^{-1} r with P = beta C (x) A (Sec. 3.2.1, Sec. 3.3.3):
+ * a Fourier-diagonal scaling by 1/(beta a(k)) with the k = 0 mode scaled by
+ * one, and the inverse Chebyshev Gram matrix across coefficients. */
+REG_API reg_status reg_precond(reg_ctx* ctx, const double* r, double* z);
+
+/* Regularisation operator out = beta (C (x) A) v (App. A). */
+REG_API reg_status reg_regularization(reg_ctx* ctx, const double* v, double* out);
+
+/* State solve m_1 = m(t=1) from m0 under v (Eq. first-order-forward). */
+REG_API reg_status reg_transport(reg_ctx* ctx, const double* v, const double* m0, double* m1);
+
+/* Adjoint of reg_transport for automatic differentiation: given G = dL/dm_1,
+ * solves the adjoint equation from lambda_1 = -G under v (state from m0) and
+ * returns grad_v = dL/dv (body force without projection, n_c*d*N; may be NULL)
+ * and grad_m0 = dL/dm0 = -lambda_0 (N; may be NULL). With the discrete
+ * quadrature both are the exact derivatives of the Heun-discretised map. */
+REG_API reg_status reg_transport_adjoint(reg_ctx* ctx, const double* v, const double* m0, const double* G,
+                                 double* grad_v, double* grad_m0);
+
+/* Deformation gradient check (App. D Eq. def-grad): F' = -(v.grad)F + (grad v)F,
+ * F_0 = I, Heun with substeps*n_t steps (substeps >= 1); stats: host double[4]
+ * = {min, max, mean, std} of det F_1; detF (may be NULL): N doubles. */
+REG_API reg_status reg_detF(reg_ctx* ctx, const double* v, int substeps, double* stats, double* detF);
+
+/* CFL number h_t * max_j max_i ||v_i(t_j)||_inf / h_x^i (Sec. 3.3.1). */
+REG_API reg_status reg_cfl(reg_ctx* ctx, const double* v, double* cfl_out);
+
+typedef struct {
+  double grad_rtol;     /* stop at ||g_k||_inf <= grad_rtol ||g_0||_inf (Sec. 3.3.5) */
+  int max_outer;        /* outer iteration cap n_opt */
+  double armijo_c1;     /* sufficient decrease constant (1e-4) */
+  double backtrack;     /* step reduction factor (0.5) */
+  int max_backtracks;   /* line search trials (20) */
+  long pcg_maxit;       /* 0 = order of the reduced system (Sec. 3.3.5) */
+  double cfl_max;       /* > 0: halve the step while the CFL number of v+s exceeds it (Sec. 3.3.5) */
+  int detF_substeps;    /* > 0: compute det F_1 statistics at the end with this many substeps */
+} reg_solve_opts;
+
+typedef struct {
+  int outer;            /* outer iterations k* */
+  long pcg_iters;       /* total PCG iterations */
+  long matvecs;         /* Hessian matvecs */
+  long n_pde;           /* hyperbolic PDE solves (Sec. 5.2) */
+  int ls_trials;        /* objective evaluations in line searches */
+  int cfl_halvings;     /* step halvings forced by the CFL bound */
+  int status;           /* reg_status of the solve */
+  double J0, J;         /* objective at v_0 and at the end */
+  double g0_inf, g_inf; /* ||g||_inf at v_0 and at the end */
+  double dist_rel;      /* ||m_1 - m_R||^2 / ||m_T - m_R||^2 (Tab. 5.1) */
+  double cfl;           /* CFL number of the final v */
+  double detF[4];       /* min, max, mean, std of det F_1 (if requested) */
+  double seconds;       /* wall time of the solve */
+} reg_solve_report;
+
+/* Fill opts with the defaults above (grad_rtol 1e-2, max_outer 50). */
+REG_API void reg_solve_opts_default(reg_solve_opts* opts);
+
+/* Inexact Gauss-Newton-Krylov solve (Alg. 1): PCG with the forcing term
+ * eta_k = min(0.5, sqrt(||g_k||_2/||g_0||_2)) (Eq. termination-criterion-ksm),
+ * preconditioner reg_precond, Armijo backtracking from alpha = 1. v_inout:
+ * initial guess in, solution out (n_c*d*N). report (may be NULL): host. */
+REG_API reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to measure the kernels).
+ * Kernel kinds: 0 row real-to-complex FFT pass, 1 row complex-to-real pass,
+ * 2 strided complex FFT pass, 3 Fourier multipliers, 4 Heun stage /
+ * transport right-hand side, 5 body-force accumulation, 6 other.
+ * ------------------------------------------------------------------------ */
+#define REG_KIND_COUNT 7
+
+/* Start bracketing every launch of the kinds in kind_mask (bit k = kind k)
+ * with CUDA events on the context's stream. */
+REG_API reg_status reg_profile_begin(reg_ctx* ctx, unsigned kind_mask);
+
+/* Stop and return, per kind (arrays of REG_KIND_COUNT, each may be NULL),
+ * the summed event time in ms, the summed algorithmic bytes (the bytes each
+ * launch must read and write) and the number of launches. Synchronises. */
+REG_API reg_status reg_profile_end(reg_ctx* ctx, double* ms, double* bytes, long* count);
+
+/* Number of kernel launches issued by the library in this process so far. */
+REG_API long reg_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

@@ -1,0 +1,145 @@
+// internal.h -- host-side declarations shared by the translation units of the
+// registration library (not part of the public C ABI, see include/reg.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+
+namespace reg {
+
+// CUDA error -> exception carrying the failing call, caught at the C ABI.
+struct CudaError {
+  cudaError_t code;
+  std::string what;
+};
+struct StatusError {
+  int status;
+  std::string what;
+};
+
+#define REG_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) throw ::reg::CudaError{e_, std::string(#call) + ": " +           \
+                                                      cudaGetErrorString(e_)};              \
+  } while (0)
+#define REG_LAUNCH()         \
+  do {                       \
+    ::reg::count_launch();   \
+    REG_CUDA(cudaGetLastError()); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Kernel accounting: a process-wide launch counter, and optional CUDA-event
+// bracketing of launches by kind (enabled per context through the C ABI).
+// ---------------------------------------------------------------------------
+enum KernelKind {
+  KK_ROWS_R2C = 0,  // real-to-complex row pass
+  KK_ROWS_C2R = 1,  // complex-to-real row pass
+  KK_COLS = 2,      // strided complex pass
+  KK_MULT = 3,      // Fourier multipliers
+  KK_STAGE = 4,     // Heun stage / transport right-hand side
+  KK_FORCE = 5,     // body-force accumulation
+  KK_OTHER = 6,     // everything else
+  KK_COUNT = 7
+};
+void count_launch();
+long launch_count();
+
+struct KernelProfiler {
+  unsigned mask = 0;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  ~KernelProfiler();
+  cudaEvent_t take();
+  void collect(double* ms, double* bytes, long* count);  // synchronises
+};
+extern thread_local KernelProfiler* tl_prof;
+
+// bracket one launch; bytes = algorithmic bytes moved by it
+struct ProfScope {
+  int kind;
+  cudaStream_t s;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(int k, cudaStream_t st, double b);
+  ~ProfScope();
+};
+
+// Periodic nodal grid, row-major with the last axis fastest. Real fields hold
+// N values; packed half spectra hold Nc = N/2 complex values laid out as
+// [n_0]..[n_{d-2}][M], M = n_{d-1}/2, where slot 0 of the last axis carries
+// uhat(k',0) + i*uhat(k',n_{d-1}/2) (DC and Nyquist columns of the last axis).
+struct Grid {
+  int d = 0;
+  int n[3] = {1, 1, 1};
+  long N = 0;   // real points
+  long Nc = 0;  // packed spectral points
+  int L = 0;    // last-axis length
+  int M = 0;    // L/2
+  long rows = 0;  // N / L
+};
+
+Grid make_grid(int d, const int64_t* n);
+
+// Batched power-of-two FFTs and Fourier multipliers on one grid, in precision T.
+template <typename T>
+class Spectral {
+ public:
+  using C = cx<T>;
+  Spectral(const Grid& g, cudaStream_t s);
+  ~Spectral();
+  Spectral(const Spectral&) = delete;
+  Spectral& operator=(const Spectral&) = delete;
+
+  const Grid& grid() const { return g_; }
+  cudaStream_t stream() const { return s_; }
+
+  // real field -> packed spectrum (unnormalised)
+  void fwd(const T* u, C* U);
+  // packed spectrum -> real field (normalised by 1/N); U is overwritten
+  void inv(C* U, T* u);
+  // G[i] = d/dx_i u, i < d  (first derivatives with the Nyquist mode dropped)
+  void grad(const T* u, T* G, C* U, C* W);
+  // out = sum_i d/dx_i q_i
+  void div(const T* q, T* out, C* U, C* S);
+  // W = i k~_axis U (W may equal U)
+  void mult_deriv(const C* U, C* W, int axis);
+  // S (+)= i k~_axis U
+  void mult_deriv_acc(const C* U, C* S, int axis, bool first);
+  // in place Leray projection of d spectra (stride Nc)
+  void mult_leray(C* W);
+
+  const C* twiddles(int L) const;   // Stockham stage tables for length L
+  const C* rc_twiddles() const;     // exp(-2 pi i k / L_last), k < M
+
+ private:
+  void cols(C* U, int axis, bool inverse);
+  Grid g_;
+  cudaStream_t s_;
+  C* tw_ = nullptr;  // device: tables per length + real/complex table
+  long tw_off_[11] = {0};  // offset of the table of length 2^e
+  long rc_off_ = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Fourier-diagonal operators on whole coefficient vectors (FP64), with the
+// DC/Nyquist pairing of the packed last-axis slot 0.
+// ---------------------------------------------------------------------------
+// out_l = beta sum_l' Cg[l][l'] a(k) V_l' + (stokes ? K F_l : F_l); F may be null.
+void spec_tail(const Grid& g, cudaStream_t s, const double2* V, const double2* F, double2* out, int nc,
+               double beta, const double* Cg_dev, int reg, int stokes);
+// out_l = sum_l' Ci[l][l'] s(k) R_l' with s = 1/(beta a(k)), s = 1 at k = 0.
+void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out, int nc, double beta,
+                  const double* Ci_dev, int reg);
+
+}  // namespace reg

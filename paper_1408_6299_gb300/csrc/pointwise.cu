@@ -1,0 +1,375 @@
+// pointwise.cu -- pointwise stages of the transport solves and the vector
+// kernels of the Krylov/Newton loops (Mang & Biros, Sec. 3.2-3.3).
+//
+// Heun's RK2 (reading of "explicit second-order Runge-Kutta", Sec. 3.3.1):
+//   k1 = F(t_j, y_j), yh = y_j + h k1, k2 = F(t_{j+1}, yh),
+//   y_{j+1} = y_j + h/2 (k1 + k2) = acc + h/2 k2 with acc = y_j + h/2 k1.
+// The stage kernels below take the spectral derivatives of the current stage
+// input and form the right-hand sides of
+//   state        m'  = -v . grad m                      (Eq. first-order-forward)
+//   incr. state  m~' = -v . grad m~ - grad m . v~        (Eq. gauss-newton)
+// together with the Runge-Kutta combination.
+#include <float.h>
+
+#include "pointwise.h"
+
+namespace reg {
+
+namespace {
+
+inline unsigned nblk(long n, int bs = 256) {
+  long b = (n + bs - 1) / bs;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T, typename S>
+__global__ void k_vel_at(const S* __restrict__ coef, int nc, Coefs b, T* __restrict__ out, long dN) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= dN) return;
+  double s = 0.0;
+  for (int l = 0; l < nc; ++l) s += b.c[l] * (double)coef[l * dN + x];
+  out[x] = (T)s;
+}
+
+template <typename S, typename T>
+__global__ void k_convert(const S* __restrict__ in, T* __restrict__ out, long n) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) out[x] = (T)in[x];
+}
+
+// k = -sum_i v_i G_i - [sum_i gm_i w_i]; Heun stage 1 or 2 update.
+template <typename T, bool SRC, bool STAGE1>
+__global__ void k_stage(const T* __restrict__ G, const T* __restrict__ vt, const T* __restrict__ gm,
+                        const T* __restrict__ wt, const T* __restrict__ y, T h, T* __restrict__ yh,
+                        T* __restrict__ acc, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  T k = 0;
+  if (G)
+    for (int i = 0; i < d; ++i) k -= vt[i * N + x] * G[i * N + x];
+  if (SRC)
+    for (int i = 0; i < d; ++i) k -= gm[i * N + x] * wt[i * N + x];
+  if (STAGE1) {
+    T yv = y ? y[x] : (T)0;
+    yh[x] = yv + h * k;
+    acc[x] = yv + (T)0.5 * h * k;
+  } else {
+    yh[x] = y[x] + (T)0.5 * h * k;  // y holds acc here; yh is the new state
+  }
+}
+
+template <typename T>
+__global__ void k_heun1(const T* __restrict__ k, const T* __restrict__ y, T h, T* __restrict__ yh,
+                        T* __restrict__ acc, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  T kv = k[x], yv = y[x];
+  yh[x] = yv + h * kv;
+  acc[x] = yv + (T)0.5 * h * kv;
+}
+
+template <typename T>
+__global__ void k_heun2(const T* __restrict__ k, const T* __restrict__ acc, T h, T* __restrict__ y, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  y[x] = acc[x] + (T)0.5 * h * k[x];
+}
+
+template <typename T>
+__global__ void k_products(const T* __restrict__ vt, const T* __restrict__ lam, T* __restrict__ q, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  T l = lam[x];
+  for (int i = 0; i < d; ++i) q[i * N + x] = vt[i * N + x] * l;
+}
+
+// f[l][i][x] += c_l lam[x] gm[i][x]   (double accumulation)
+template <typename T>
+__global__ void k_force(double* __restrict__ f, const T* __restrict__ lam, const T* __restrict__ gm, Coefs c,
+                        int nc, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  double l = (double)lam[x];
+  for (int i = 0; i < d; ++i) {
+    double p = l * (double)gm[i * N + x];
+    for (int a = 0; a < nc; ++a) f[((long)a * d + i) * N + x] += c.c[a] * p;
+  }
+}
+
+// det F right-hand side for component q = (a,c): -v.grad F_q + sum_m gv_{am} F_{mc}
+__global__ void k_detF_rhs(const double* __restrict__ G, const double* __restrict__ vt,
+                           const double* __restrict__ gv, const double* __restrict__ F, int q, double* __restrict__ k,
+                           int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  int a = q / d, c = q % d;
+  double s = 0.0;
+  for (int i = 0; i < d; ++i) s -= vt[i * N + x] * G[i * N + x];
+  for (int m = 0; m < d; ++m) s += gv[(a * d + m) * N + x] * F[(m * d + c) * N + x];
+  k[q * N + x] = s;
+}
+
+__global__ void k_identity_tensor(double* __restrict__ F, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  for (int a = 0; a < d; ++a)
+    for (int c = 0; c < d; ++c) F[(a * d + c) * N + x] = (a == c) ? 1.0 : 0.0;
+}
+
+__global__ void k_det(const double* __restrict__ F, double* __restrict__ det, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  if (d == 2) {
+    det[x] = F[x] * F[3 * N + x] - F[N + x] * F[2 * N + x];
+  } else {
+    double a00 = F[x], a01 = F[N + x], a02 = F[2 * N + x];
+    double a10 = F[3 * N + x], a11 = F[4 * N + x], a12 = F[5 * N + x];
+    double a20 = F[6 * N + x], a21 = F[7 * N + x], a22 = F[8 * N + x];
+    det[x] = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+  }
+}
+
+template <typename T>
+__global__ void k_lincomb_t(T a, const T* __restrict__ x, T b, const T* __restrict__ y, T* __restrict__ out, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + (y ? b * y[i] : (T)0);
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_lincomb(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double* __restrict__ out, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: fixed grid, fixed per-thread striding, block tree
+// in shared memory, then one block combines the partials in index order.
+// ---------------------------------------------------------------------------
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+enum RedOp { RED_DOT = 0, RED_SQDIFF = 1, RED_MAXABS = 2, RED_STATS = 3 };
+
+struct Acc4 {
+  double s, s2, mn, mx;
+};
+
+template <int OP>
+__global__ void k_reduce(const double* __restrict__ a, const double* __restrict__ b, long n, double center,
+                         double* __restrict__ part) {
+  __shared__ double sh[4][kRedThreads];
+  double s = 0, s2 = 0, mn = DBL_MAX, mx = -DBL_MAX;
+  for (long i = (long)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (long)kRedBlocks * kRedThreads) {
+    double x = a[i];
+    if (OP == RED_DOT) s += x * b[i];
+    else if (OP == RED_SQDIFF) { double t = x - b[i]; s += t * t; }
+    else if (OP == RED_MAXABS) mx = fmax(mx, fabs(x));
+    else { double t = x - center; s += t; s2 += t * t; mn = fmin(mn, x); mx = fmax(mx, x); }
+  }
+  sh[0][threadIdx.x] = s;
+  sh[1][threadIdx.x] = s2;
+  sh[2][threadIdx.x] = mn;
+  sh[3][threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+      sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[k * kRedBlocks + blockIdx.x] = sh[k][0];
+}
+
+__global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[4][kRedThreads];
+  double s = 0, s2 = 0, mn = DBL_MAX, mx = -DBL_MAX;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) {
+    s += part[i];
+    s2 += part[kRedBlocks + i];
+    mn = fmin(mn, part[2 * kRedBlocks + i]);
+    mx = fmax(mx, part[3 * kRedBlocks + i]);
+  }
+  sh[0][threadIdx.x] = s;
+  sh[1][threadIdx.x] = s2;
+  sh[2][threadIdx.x] = mn;
+  sh[3][threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+      sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) out[k] = sh[k][0];
+}
+
+}  // namespace
+
+template <typename T, typename S>
+void vel_at(const S* coef, int nc, const Coefs& b, T* out, long dN, cudaStream_t s) {
+  k_vel_at<T, S><<<nblk(dN), 256, 0, s>>>(coef, nc, b, out, dN);
+  REG_LAUNCH();
+}
+template void vel_at<float, double>(const double*, int, const Coefs&, float*, long, cudaStream_t);
+template void vel_at<double, double>(const double*, int, const Coefs&, double*, long, cudaStream_t);
+template void vel_at<float, float>(const float*, int, const Coefs&, float*, long, cudaStream_t);
+
+template <typename S, typename T>
+void convert(const S* in, T* out, long n, cudaStream_t s) {
+  k_convert<S, T><<<nblk(n), 256, 0, s>>>(in, out, n);
+  REG_LAUNCH();
+}
+template void convert<double, float>(const double*, float*, long, cudaStream_t);
+template void convert<float, double>(const float*, double*, long, cudaStream_t);
+template void convert<double, double>(const double*, double*, long, cudaStream_t);
+
+template <typename T>
+void transport_stage1(const T* G, const T* vt, const T* gm, const T* wt, const T* y, T h, T* yh, T* acc, int d,
+                      long N, cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * ((G ? 2 * d : 0) + (gm ? 2 * d : 0) + (y ? 1 : 0) + 2));
+  if (gm) k_stage<T, true, true><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, y, h, yh, acc, d, N);
+  else k_stage<T, false, true><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, y, h, yh, acc, d, N);
+  REG_LAUNCH();
+}
+template <typename T>
+void transport_stage2(const T* G, const T* vt, const T* gm, const T* wt, const T* acc, T h, T* ynew, int d, long N,
+                      cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + (gm ? 2 * d : 0) + 2));
+  if (gm) k_stage<T, true, false><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, acc, h, ynew, nullptr, d, N);
+  else k_stage<T, false, false><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, acc, h, ynew, nullptr, d, N);
+  REG_LAUNCH();
+}
+template <typename T>
+void heun1(const T* k, const T* y, T h, T* yh, T* acc, long N, cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, 4.0 * N * sizeof(T));
+  k_heun1<T><<<nblk(N), 256, 0, s>>>(k, y, h, yh, acc, N);
+  REG_LAUNCH();
+}
+template <typename T>
+void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, 3.0 * N * sizeof(T));
+  k_heun2<T><<<nblk(N), 256, 0, s>>>(k, acc, h, y, N);
+  REG_LAUNCH();
+}
+template <typename T>
+void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + 1));
+  k_products<T><<<nblk(N), 256, 0, s>>>(vt, lam, q, d, N);
+  REG_LAUNCH();
+}
+template <typename T>
+void force_acc(double* f, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s) {
+  ProfScope ps(KK_FORCE, s, (double)N * (sizeof(T) * (d + 1) + 16.0 * nc * d));
+  k_force<T><<<nblk(N), 256, 0, s>>>(f, lam, gm, c, nc, d, N);
+  REG_LAUNCH();
+}
+
+#define INST(T)                                                                                          \
+  template void transport_stage1<T>(const T*, const T*, const T*, const T*, const T*, T, T*, T*, int, long, \
+                                    cudaStream_t);                                                       \
+  template void transport_stage2<T>(const T*, const T*, const T*, const T*, const T*, T, T*, int, long,     \
+                                    cudaStream_t);                                                       \
+  template void heun1<T>(const T*, const T*, T, T*, T*, long, cudaStream_t);                                \
+  template void heun2<T>(const T*, const T*, T, T*, long, cudaStream_t);                                    \
+  template void products<T>(const T*, const T*, T*, int, long, cudaStream_t);                               \
+  template void force_acc<T>(double*, const T*, const T*, const Coefs&, int, int, long, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+template <typename T>
+void lincomb_t(T a, const T* x, T b, const T* y, T* out, long n, cudaStream_t s) {
+  k_lincomb_t<T><<<nblk(n), 256, 0, s>>>(a, x, b, y, out, n);
+  REG_LAUNCH();
+}
+template void lincomb_t<float>(float, const float*, float, const float*, float*, long, cudaStream_t);
+template void lincomb_t<double>(double, const double*, double, const double*, double*, long, cudaStream_t);
+
+void detF_rhs(const double* G, const double* vt, const double* gv, const double* F, int q, double* k, int d, long N,
+              cudaStream_t s) {
+  k_detF_rhs<<<nblk(N), 256, 0, s>>>(G, vt, gv, F, q, k, d, N);
+  REG_LAUNCH();
+}
+void identity_tensor(double* F, int d, long N, cudaStream_t s) {
+  k_identity_tensor<<<nblk(N), 256, 0, s>>>(F, d, N);
+  REG_LAUNCH();
+}
+void det_tensor(const double* F, double* det, int d, long N, cudaStream_t s) {
+  k_det<<<nblk(N), 256, 0, s>>>(F, det, d, N);
+  REG_LAUNCH();
+}
+void axpby(double a, const double* x, double b, double* y, long n, cudaStream_t s) {
+  k_axpby<<<nblk(n), 256, 0, s>>>(a, x, b, y, n);
+  REG_LAUNCH();
+}
+void lincomb(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s) {
+  k_lincomb<<<nblk(n), 256, 0, s>>>(a, x, b, y, out, n);
+  REG_LAUNCH();
+}
+
+long reduce_scratch_doubles() { return 4L * kRedBlocks + 4; }
+
+// result (device, 4 doubles at scratch + 4*kRedBlocks): {sum, sumsq, min, max}
+static double* launch_reduce(int op, const double* a, const double* b, long n, double* scratch, cudaStream_t s,
+                             double center = 0.0) {
+  double* out = scratch + 4L * kRedBlocks;
+  switch (op) {
+    case RED_DOT: k_reduce<RED_DOT><<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, 0.0, scratch); break;
+    case RED_SQDIFF: k_reduce<RED_SQDIFF><<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, 0.0, scratch); break;
+    case RED_MAXABS: k_reduce<RED_MAXABS><<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, 0.0, scratch); break;
+    default: k_reduce<RED_STATS><<<kRedBlocks, kRedThreads, 0, s>>>(a, b, n, center, scratch); break;
+  }
+  REG_LAUNCH();
+  k_reduce_final<<<1, kRedThreads, 0, s>>>(scratch, out);
+  REG_LAUNCH();
+  return out;
+}
+
+static void fetch(const double* dev, double* host, int count, cudaStream_t s) {
+  REG_CUDA(cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+  REG_CUDA(cudaStreamSynchronize(s));
+}
+
+double dot(const double* a, const double* b, long n, double* scratch, cudaStream_t s) {
+  double r[4];
+  fetch(launch_reduce(RED_DOT, a, b, n, scratch, s), r, 4, s);
+  return r[0];
+}
+double sqdiff(const double* a, const double* b, long n, double* scratch, cudaStream_t s) {
+  double r[4];
+  fetch(launch_reduce(RED_SQDIFF, a, b, n, scratch, s), r, 4, s);
+  return r[0];
+}
+double maxabs(const double* a, long n, double* scratch, cudaStream_t s) {
+  double r[4];
+  fetch(launch_reduce(RED_MAXABS, a, nullptr, n, scratch, s), r, 4, s);
+  return r[3];
+}
+// {min, max, mean, std}: two passes, the second centred on the mean
+void stats(const double* a, long n, double* scratch, cudaStream_t s, double out[4]) {
+  double r[4];
+  fetch(launch_reduce(RED_STATS, a, nullptr, n, scratch, s, 0.0), r, 4, s);
+  double mean = r[0] / n;
+  fetch(launch_reduce(RED_STATS, a, nullptr, n, scratch, s, mean), r, 4, s);
+  double c = r[0] / n;
+  double var = r[1] / n - c * c;
+  out[0] = r[2];
+  out[1] = r[3];
+  out[2] = mean + c;
+  out[3] = var > 0 ? sqrt(var) : 0.0;
+}
+
+}  // namespace reg

@@ -1,0 +1,60 @@
+// pointwise.h -- launchers of the pointwise transport stages, vector kernels
+// and deterministic FP64 reductions (pointwise.cu).
+#pragma once
+#include "internal.h"
+
+namespace reg {
+
+// small coefficient table passed by value (Chebyshev values, quadrature weights)
+struct Coefs {
+  double c[16];
+};
+
+// out[x] = sum_l b_l coef[l*dN + x], x < dN
+template <typename T, typename S>
+void vel_at(const S* coef, int nc, const Coefs& b, T* out, long dN, cudaStream_t s);
+template <typename S, typename T>
+void convert(const S* in, T* out, long n, cudaStream_t s);
+
+// Heun stage 1 of m' = -v.G - gm.w (the gm.w source only when gm != null; G may
+// be null for a zero state; y may be null for a zero state):
+//   yh = y + h k, acc = y + h/2 k.
+template <typename T>
+void transport_stage1(const T* G, const T* vt, const T* gm, const T* wt, const T* y, T h, T* yh, T* acc, int d,
+                      long N, cudaStream_t s);
+// Heun stage 2: ynew = acc + h/2 k.
+template <typename T>
+void transport_stage2(const T* G, const T* vt, const T* gm, const T* wt, const T* acc, T h, T* ynew, int d, long N,
+                      cudaStream_t s);
+template <typename T>
+void heun1(const T* k, const T* y, T h, T* yh, T* acc, long N, cudaStream_t s);
+template <typename T>
+void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s);
+// q_i = v_i lam
+template <typename T>
+void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s);
+// f[l][i] += c_l lam gm_i in double precision
+template <typename T>
+void force_acc(double* f, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s);
+
+void detF_rhs(const double* G, const double* vt, const double* gv, const double* F, int q, double* k, int d, long N,
+              cudaStream_t s);
+void identity_tensor(double* F, int d, long N, cudaStream_t s);
+void det_tensor(const double* F, double* det, int d, long N, cudaStream_t s);
+
+// out = a x + b y in precision T (y may be null: out = a x; out may alias x or y)
+template <typename T>
+void lincomb_t(T a, const T* x, T b, const T* y, T* out, long n, cudaStream_t s);
+
+// y = a x + b y ; out = a x + b y
+void axpby(double a, const double* x, double b, double* y, long n, cudaStream_t s);
+void lincomb(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s);
+
+// reductions (synchronise the stream; scratch holds reduce_scratch_doubles())
+long reduce_scratch_doubles();
+double dot(const double* a, const double* b, long n, double* scratch, cudaStream_t s);
+double sqdiff(const double* a, const double* b, long n, double* scratch, cudaStream_t s);
+double maxabs(const double* a, long n, double* scratch, cudaStream_t s);
+void stats(const double* a, long n, double* scratch, cudaStream_t s, double out[4]);
+
+}  // namespace reg

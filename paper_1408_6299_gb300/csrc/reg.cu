@@ -1,0 +1,985 @@
+// reg.cu -- context, transport sweeps, reduced-space operators and the
+// inexact Gauss-Newton-Krylov solve behind the C ABI of include/reg.h
+// (Mang & Biros, arXiv:1408.6299: Alg. 1 outer iteration, Alg. 2 Hessian
+// matvec, Sec. 3.2-3.3 discretisation and preconditioning).
+//
+// Time stepping is Heun's RK2 on the nodes t_j = j/n_t. A sweep reads the
+// velocity v(t_j) = sum_l T_l(2 t_j - 1) v_l (Sec. 3.3.2) at the two nodes of a
+// step. The state gradients grad m_j are either stored for every node
+// (ckpt_every = 0) or recomputed segment by segment from every K-th state
+// (ckpt_every = K). The body-force time integral uses the trapezoid rule on
+// the nodes (default) or the stage values of the discrete adjoint.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/reg.h"
+#include "internal.h"
+#include "pointwise.h"
+
+using namespace reg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// device buffer owned by the context
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  T* get(size_t count) {
+    if (count <= n && p) return p;
+    release();
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw StatusError{REG_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+    return p;
+  }
+};
+
+// Chebyshev polynomials T_l(x) by the three-term recurrence
+void cheb_values(int nc, double t, double* b) {
+  double x = 2.0 * t - 1.0;
+  for (int l = 0; l < nc; ++l) b[l] = l == 0 ? 1.0 : (l == 1 ? x : 2.0 * x * b[l - 1] - b[l - 2]);
+}
+
+// exact int_0^1 T_a(2t-1) T_b(2t-1) dt via T_a T_b = (T_{a+b} + T_{|a-b|})/2
+double cheb_gram_entry(int a, int b) {
+  auto I = [](int m) { return (m % 2) ? 0.0 : 2.0 / (1.0 - (double)m * (double)m); };
+  return 0.25 * (I(a + b) + I(a > b ? a - b : b - a));
+}
+
+bool invert_small(int n, const std::vector<double>& A, std::vector<double>& Ai) {
+  std::vector<double> M(n * 2 * n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) M[r * 2 * n + c] = c < n ? A[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(M[r * 2 * n + c]) > std::fabs(M[piv * 2 * n + c])) piv = r;
+    if (M[piv * 2 * n + c] == 0.0) return false;
+    for (int k = 0; k < 2 * n; ++k) std::swap(M[c * 2 * n + k], M[piv * 2 * n + k]);
+    double p = M[c * 2 * n + c];
+    for (int k = 0; k < 2 * n; ++k) M[c * 2 * n + k] /= p;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        double f = M[r * 2 * n + c];
+        for (int k = 0; k < 2 * n; ++k) M[r * 2 * n + k] -= f * M[c * 2 * n + k];
+      }
+  }
+  Ai.assign(n * n, 0.0);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) Ai[r * n + c] = M[r * 2 * n + n + c];
+  return true;
+}
+
+// per-precision scratch of the sweeps
+template <typename T>
+struct Work {
+  using C = cx<T>;
+  DBuf<C> U, W;            // spectra
+  DBuf<T> G, q, va, vb, wa, wb;  // d fields
+  DBuf<T> m, yh, acc, k, lam;    // fields
+  DBuf<T> vcoef, wcoef;          // coefficient vectors in precision T
+  DBuf<T> gm, gmh, ck;           // state gradients (all nodes or one segment), stage gradients, checkpoints
+};
+
+}  // namespace
+
+struct reg_ctx {
+  int d = 0, n_t = 0, n_c = 0, rtype = 1, stokes = 0, prec = 0, ckpt = 0, quad = 0;
+  double beta = 0;
+  cudaStream_t s = nullptr;
+  Grid g;
+  double hd = 1.0;  // cell volume
+  std::string err;
+
+  std::vector<double> bnode;  // (n_t+1) x n_c basis values at the nodes
+  std::vector<double> Cg, Ci;
+  DBuf<double> Cg_dev, Ci_dev;
+
+  std::unique_ptr<Spectral<double>> sp64;
+  std::unique_ptr<Spectral<float>> sp32;
+  Work<double> w64;
+  Work<float> w32;
+
+  DBuf<double> mT, mR;
+  bool have_images = false;
+  bool ready = false;  // linearisation point set (stored state valid)
+  DBuf<double> vlin;   // linearisation point
+
+  DBuf<double> f;      // body force (n_c d N)
+  DBuf<double2> SV, SF;  // spectra of coefficient vectors for the tail
+  DBuf<double> red;    // reduction scratch
+  DBuf<double> tmpA, tmpB;  // coefficient-vector temporaries
+  DBuf<double> stage_in[3], stage_out;  // staging of host arrays
+  // det F scratch
+  DBuf<double> F, Fh, K1, K2, gvl, gvt, det;
+  // solve vectors
+  DBuf<double> sv_g, sv_s, sv_r, sv_z, sv_p, sv_Hp, sv_vt;
+  KernelProfiler prof;  // CUDA-event bracketing of launches by kind (off unless enabled)
+
+  long N() const { return g.N; }
+  long ncdN() const { return (long)n_c * d * g.N; }
+  long dN() const { return (long)d * g.N; }
+  double h() const { return 1.0 / n_t; }
+  Coefs basis_at_node(int j, double scale = 1.0) const {
+    Coefs c{};
+    for (int l = 0; l < n_c; ++l) c.c[l] = scale * bnode[(size_t)j * n_c + l];
+    return c;
+  }
+  double trap_w(int j) const { return (j == 0 || j == n_t) ? 0.5 * h() : h(); }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// host/device pointer handling
+// ---------------------------------------------------------------------------
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+const double* input_ptr(reg_ctx* c, const double* p, long n, int slot) {
+  if (!p) throw StatusError{REG_EINVAL, "null array argument"};
+  if (is_device_ptr(p)) return p;
+  double* d = c->stage_in[slot].get(n);
+  REG_CUDA(cudaMemcpyAsync(d, p, n * sizeof(double), cudaMemcpyHostToDevice, c->s));
+  return d;
+}
+
+struct Output {
+  reg_ctx* c;
+  double* user;
+  double* dev;
+  long n;
+  bool host;
+  Output(reg_ctx* c_, double* p, long n_, DBuf<double>& stage) : c(c_), user(p), n(n_) {
+    if (!p) throw StatusError{REG_EINVAL, "null output argument"};
+    host = !is_device_ptr(p);
+    dev = host ? stage.get(n) : p;
+  }
+  void finish() {
+    if (host) REG_CUDA(cudaMemcpyAsync(user, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    REG_CUDA(cudaStreamSynchronize(c->s));
+  }
+};
+
+template <typename T>
+Work<T>& work(reg_ctx* c);
+template <>
+Work<double>& work<double>(reg_ctx* c) { return c->w64; }
+template <>
+Work<float>& work<float>(reg_ctx* c) { return c->w32; }
+template <typename T>
+Spectral<T>& spectral(reg_ctx* c);
+template <>
+Spectral<double>& spectral<double>(reg_ctx* c) { return *c->sp64; }
+template <>
+Spectral<float>& spectral<float>(reg_ctx* c) {
+  if (!c->sp32) c->sp32.reset(new Spectral<float>(c->g, c->s));
+  return *c->sp32;
+}
+
+template <typename T>
+void grad_into(reg_ctx* c, const T* u, T* G) {
+  Work<T>& w = work<T>(c);
+  spectral<T>(c).grad(u, G, w.U.get(c->g.Nc), w.W.get(c->g.Nc));
+}
+
+// velocity (coefficients in precision T) at node j: a pointer to d fields
+template <typename T>
+const T* vel_node(reg_ctx* c, const T* coef, int j, T* buf) {
+  if (c->n_c == 1) return coef;
+  vel_at<T, T>(coef, c->n_c, c->basis_at_node(j), buf, c->dN(), c->s);
+  return buf;
+}
+
+// div(v lam) into out
+template <typename T>
+void div_vlam(reg_ctx* c, const T* vt, const T* lam, T* out) {
+  Work<T>& w = work<T>(c);
+  T* q = w.q.get(c->dN());
+  products<T>(vt, lam, q, c->d, c->N(), c->s);
+  spectral<T>(c).div(q, out, w.U.get(c->g.Nc), w.W.get(c->g.Nc));
+}
+
+// ---------------------------------------------------------------------------
+// State solve (Eq. first-order-forward), steps j0..j1-1 from the state in w.m.
+//   gm  (optional): grad m_j into slot (j - base) for j = j0..j1 (the last slot
+//                   is the extra gradient of the final state)
+//   gmh (optional): grad of the stage-2 input of step j into slot (j+1 - base)
+//   ck  (optional): m_j into slot j/K for j % K == 0 (and the final state)
+// ---------------------------------------------------------------------------
+template <typename T>
+void state_steps(reg_ctx* c, const T* vcoef, int j0, int j1, T* gm, T* gmh, int base, T* ck) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  const T h = (T)c->h();
+  T* m = w.m.get(N);
+  T* yh = w.yh.get(N);
+  T* acc = w.acc.get(N);
+  T* G = w.G.get(dN);
+  T* va = w.va.get(dN);
+  T* vb = w.vb.get(dN);
+  for (int j = j0; j < j1; ++j) {
+    if (ck && c->ckpt > 0 && j % c->ckpt == 0)
+      REG_CUDA(cudaMemcpyAsync(ck + (long)(j / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+    T* G1 = gm ? gm + (long)(j - base) * dN : G;
+    grad_into<T>(c, m, G1);
+    transport_stage1<T>(G1, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, h, yh, acc, c->d, N, c->s);
+    T* G2 = gmh ? gmh + (long)(j + 1 - base) * dN : G;
+    grad_into<T>(c, yh, G2);
+    transport_stage2<T>(G2, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, h, m, c->d, N, c->s);
+  }
+  if (ck && c->ckpt > 0 && j1 % c->ckpt == 0)
+    REG_CUDA(cudaMemcpyAsync(ck + (long)(j1 / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  if (gm) grad_into<T>(c, m, gm + (long)(j1 - base) * dN);
+}
+
+// Recompute state gradients of segment [j0, j1] from the checkpoint at j0.
+template <typename T>
+void recompute_segment(reg_ctx* c, const T* vcoef, int j0, int j1) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  T* m = w.m.get(N);
+  REG_CUDA(cudaMemcpyAsync(m, w.ck.p + (long)(j0 / c->ckpt) * N, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  state_steps<T>(c, vcoef, j0, j1, w.gm.get((size_t)(c->ckpt + 1) * dN),
+                 c->quad ? w.gmh.get((size_t)(c->ckpt + 1) * dN) : nullptr, j0, nullptr);
+}
+
+// Gradient slots available for node j (after ensure_segment)
+template <typename T>
+const T* gm_slot(reg_ctx* c, int j, int base) {
+  return work<T>(c).gm.p + (long)(j - base) * c->dN();
+}
+template <typename T>
+const T* gmh_slot(reg_ctx* c, int j, int base) {
+  return work<T>(c).gmh.p + (long)(j - base) * c->dN();
+}
+
+// Full state solve from m0 with storage for later sweeps (store-all or checkpoints).
+template <typename T>
+void state_solve_store(reg_ctx* c, const T* vcoef, const T* m0) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  REG_CUDA(cudaMemcpyAsync(w.m.get(N), m0, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  if (c->ckpt == 0) {
+    state_steps<T>(c, vcoef, 0, c->n_t, w.gm.get((size_t)(c->n_t + 1) * dN),
+                   c->quad ? w.gmh.get((size_t)(c->n_t + 1) * dN) : nullptr, 0, nullptr);
+  } else {
+    state_steps<T>(c, vcoef, 0, c->n_t, nullptr, nullptr, 0, w.ck.get((size_t)(c->n_t / c->ckpt + 1) * N));
+  }
+}
+
+// Adjoint solve (Eq. first-order-adjoint) backward from lam (in w.lam at n_t),
+// accumulating the body force f_l = int b_l lam grad m dt (double) into f.
+// Leaves lam_0 in w.lam.
+template <typename T>
+void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  const double hd = c->h();
+  const T h = (T)hd;
+  T* lam = w.lam.p;
+  T* yh = w.yh.get(N);
+  T* acc = w.acc.get(N);
+  T* k = w.k.get(N);
+  T* va = w.va.get(dN);
+  T* vb = w.vb.get(dN);
+  REG_CUDA(cudaMemsetAsync(f, 0, c->ncdN() * sizeof(double), c->s));
+  const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
+  for (int seg = (c->n_t - 1) / K; seg >= 0; --seg) {
+    int j0 = seg * K, j1 = j0 + K;
+    int base = 0;
+    if (c->ckpt > 0) {
+      recompute_segment<T>(c, vcoef, j0, j1);
+      base = j0;
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      if (!c->quad)
+        force_acc<T>(f, lam, gm_slot<T>(c, j + 1, base), c->basis_at_node(j + 1, c->trap_w(j + 1)), c->n_c, c->d, N,
+                     c->s);
+      else
+        force_acc<T>(f, lam, gmh_slot<T>(c, j + 1, base), c->basis_at_node(j + 1, 0.5 * hd), c->n_c, c->d, N, c->s);
+      div_vlam<T>(c, vel_node<T>(c, vcoef, j + 1, vb), lam, k);
+      heun1<T>(k, lam, h, yh, acc, N, c->s);
+      if (c->quad)
+        force_acc<T>(f, yh, gm_slot<T>(c, j, base), c->basis_at_node(j, 0.5 * hd), c->n_c, c->d, N, c->s);
+      div_vlam<T>(c, vel_node<T>(c, vcoef, j, va), yh, k);
+      heun2<T>(k, acc, h, lam, N, c->s);
+    }
+    if (j0 == 0 && !c->quad)
+      force_acc<T>(f, lam, gm_slot<T>(c, 0, base), c->basis_at_node(0, c->trap_w(0)), c->n_c, c->d, N, c->s);
+  }
+}
+
+// Incremental state solve forward from 0 (Eq. gauss-newton, first line), then
+// the incremental adjoint backward from -m~_1 with the incremental body force.
+template <typename T>
+void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  const T h = (T)c->h();
+  T* y = w.lam.get(N);  // the incremental state ends up as -lam~_1 in place
+  T* yh = w.yh.get(N);
+  T* acc = w.acc.get(N);
+  T* G = w.G.get(dN);
+  T* va = w.va.get(dN);
+  T* vb = w.vb.get(dN);
+  T* wa = w.wa.get(dN);
+  T* wb = w.wb.get(dN);
+  const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
+  for (int seg = 0; seg * K < c->n_t; ++seg) {
+    int j0 = seg * K, j1 = j0 + K;
+    int base = 0;
+    if (c->ckpt > 0) {
+      recompute_segment<T>(c, vcoef, j0, j1);
+      base = j0;
+    }
+    for (int j = j0; j < j1; ++j) {
+      const T* g1 = gm_slot<T>(c, j, base);
+      const T* g2 = c->quad ? gmh_slot<T>(c, j + 1, base) : gm_slot<T>(c, j + 1, base);
+      const T* vA = vel_node<T>(c, vcoef, j, va);
+      const T* wA = vel_node<T>(c, wcoef, j, wa);
+      if (j == 0) {
+        transport_stage1<T>(nullptr, vA, g1, wA, nullptr, h, yh, acc, c->d, N, c->s);
+      } else {
+        grad_into<T>(c, y, G);
+        transport_stage1<T>(G, vA, g1, wA, y, h, yh, acc, c->d, N, c->s);
+      }
+      grad_into<T>(c, yh, G);
+      transport_stage2<T>(G, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, h, y, c->d,
+                          N, c->s);
+    }
+  }
+  // lam~_1 = -m~_1
+  lincomb_t<T>((T)-1, y, (T)0, nullptr, y, N, c->s);
+  adjoint_solve<T>(c, vcoef, f);
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Fourier-diagonal tail (FP64): out = beta (C (x) A) V + K^gamma F
+// (App. A Eq. control-equation-expansion; Eq. eliminated-control). F may be null.
+// ---------------------------------------------------------------------------
+void tail(reg_ctx* c, const double* V, const double* F, double* out) {
+  const long Nc = c->g.Nc, N = c->N();
+  const int ncd = c->n_c * c->d;
+  double2* SV = c->SV.get((size_t)ncd * Nc);
+  double2* SF = c->SF.get((size_t)ncd * Nc);
+  Spectral<double>& sp = *c->sp64;
+  for (int q = 0; q < ncd; ++q) {
+    sp.fwd(V + q * N, SV + q * Nc);
+    if (F) sp.fwd(F + q * N, SF + q * Nc);
+  }
+  spec_tail(c->g, c->s, SV, F ? SF : nullptr, SF, c->n_c, c->beta, c->Cg_dev.p, c->rtype, c->stokes);
+  for (int q = 0; q < ncd; ++q) sp.inv(SF + q * Nc, out + q * N);
+}
+
+void precond(reg_ctx* c, const double* r, double* z) {
+  const long Nc = c->g.Nc, N = c->N();
+  const int ncd = c->n_c * c->d;
+  double2* SV = c->SV.get((size_t)ncd * Nc);
+  double2* SF = c->SF.get((size_t)ncd * Nc);
+  Spectral<double>& sp = *c->sp64;
+  for (int q = 0; q < ncd; ++q) sp.fwd(r + q * N, SV + q * Nc);
+  spec_precond(c->g, c->s, SV, SF, c->n_c, c->beta, c->Ci_dev.p, c->rtype);
+  for (int q = 0; q < ncd; ++q) sp.inv(SF + q * Nc, z + q * N);
+}
+
+double* red(reg_ctx* c) { return c->red.get(reduce_scratch_doubles()); }
+
+// beta/2 sum_ll' c_ll' <B v_l, B v_l'>_h
+double reg_term(reg_ctx* c, const double* v) {
+  double* Rv = c->tmpB.get(c->ncdN());
+  tail(c, v, nullptr, Rv);
+  return 0.5 * c->hd * dot(v, Rv, c->ncdN(), red(c), c->s);
+}
+
+void objective(reg_ctx* c, const double* v, double parts[2]) {
+  if (!c->have_images) throw StatusError{REG_EINVAL, "reg_set_images has not been called"};
+  const long N = c->N();
+  Work<double>& w = c->w64;
+  REG_CUDA(cudaMemcpyAsync(w.m.get(N), c->mT.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  state_steps<double>(c, v, 0, c->n_t, nullptr, nullptr, 0, nullptr);
+  parts[0] = 0.5 * c->hd * sqdiff(c->mR.p, w.m.p, N, red(c), c->s);
+  parts[1] = reg_term(c, v);
+}
+
+// FP32 copies of the stored state for the mixed-precision matvec
+void prepare_mixed(reg_ctx* c) {
+  if (c->prec != REG_MIXED) return;
+  Work<double>& w = c->w64;
+  Work<float>& x = c->w32;
+  const long dN = c->dN(), N = c->N();
+  spectral<float>(c);
+  convert<double, float>(c->vlin.p, x.vcoef.get(c->ncdN()), c->ncdN(), c->s);
+  if (c->ckpt == 0) {
+    convert<double, float>(w.gm.p, x.gm.get((size_t)(c->n_t + 1) * dN), (long)(c->n_t + 1) * dN, c->s);
+    if (c->quad) convert<double, float>(w.gmh.p, x.gmh.get((size_t)(c->n_t + 1) * dN), (long)(c->n_t + 1) * dN, c->s);
+  } else {
+    long nck = c->n_t / c->ckpt + 1;
+    convert<double, float>(w.ck.p, x.ck.get((size_t)nck * N), nck * N, c->s);
+  }
+}
+
+void set_point(reg_ctx* c, const double* v) {
+  if (!c->have_images) throw StatusError{REG_EINVAL, "reg_set_images has not been called"};
+  c->ready = false;
+  REG_CUDA(cudaMemcpyAsync(c->vlin.get(c->ncdN()), v, c->ncdN() * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  state_solve_store<double>(c, c->vlin.p, c->mT.p);
+}
+
+void check_finite(double x, const char* what) {
+  if (!std::isfinite(x)) throw StatusError{REG_ENONFINITE, std::string(what) + " is not finite"};
+}
+
+// gradient at v; parts = {distance, regularisation}
+void gradient(reg_ctx* c, const double* v, double* g, double parts[2]) {
+  const long N = c->N();
+  set_point(c, v);
+  Work<double>& w = c->w64;
+  // w.m holds m_1 after the state solve
+  parts[0] = 0.5 * c->hd * sqdiff(c->mR.p, w.m.p, N, red(c), c->s);
+  lincomb_t<double>(1.0, c->mR.p, -1.0, w.m.p, w.lam.get(N), N, c->s);  // lam_1 = m_R - m_1
+  double* f = c->f.get(c->ncdN());
+  adjoint_solve<double>(c, c->vlin.p, f);
+  tail(c, c->vlin.p, f, g);
+  parts[1] = reg_term(c, c->vlin.p);
+  check_finite(parts[0] + parts[1], "objective");
+  check_finite(dot(g, g, c->ncdN(), red(c), c->s), "gradient norm");
+  prepare_mixed(c);
+  c->ready = true;
+}
+
+void hessvec(reg_ctx* c, const double* vt, double* out) {
+  if (!c->ready) throw StatusError{REG_ENOTREADY, "no linearisation point: call reg_gradient or reg_linearize first"};
+  double* f = c->f.get(c->ncdN());
+  if (c->prec == REG_FP64) {
+    gn_sweeps<double>(c, c->vlin.p, vt, f);
+  } else {
+    float* w32 = c->w32.wcoef.get(c->ncdN());
+    convert<double, float>(vt, w32, c->ncdN(), c->s);
+    gn_sweeps<float>(c, c->w32.vcoef.p, w32, f);
+  }
+  tail(c, vt, f, out);
+}
+
+Coefs basis_at(const reg_ctx* c, double t) {
+  Coefs b{};
+  cheb_values(c->n_c, t, b.c);
+  return b;
+}
+
+double cfl(reg_ctx* c, const double* v) {
+  const long N = c->N(), dN = c->dN();
+  double* vt = c->tmpA.get(dN);
+  double mx = 0.0;
+  int nodes = c->n_c == 1 ? 1 : c->n_t + 1;
+  for (int j = 0; j < nodes; ++j) {
+    const double* vj = v;
+    if (c->n_c > 1) {
+      vel_at<double, double>(v, c->n_c, c->basis_at_node(j), vt, dN, c->s);
+      vj = vt;
+    }
+    for (int i = 0; i < c->d; ++i) {
+      double hx = 2.0 * M_PI / c->g.n[i];
+      mx = std::max(mx, maxabs(vj + i * N, N, red(c), c->s) / hx);
+    }
+  }
+  return c->h() * mx;
+}
+
+// det F_1 (App. D Eq. def-grad) with substeps * n_t Heun steps
+void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_out) {
+  const long N = c->N(), dN = c->dN();
+  const int d = c->d, dd = d * d, nc = c->n_c;
+  const long ddN = (long)dd * N;
+  double* gvl = c->gvl.get((size_t)nc * ddN);
+  for (int l = 0; l < nc; ++l)
+    for (int i = 0; i < d; ++i) grad_into<double>(c, v + ((long)l * d + i) * N, gvl + ((long)l * dd + i * d) * N);
+  double* F = c->F.get(ddN);
+  double* Fh = c->Fh.get(ddN);
+  double* K1 = c->K1.get(ddN);
+  double* K2 = c->K2.get(ddN);
+  double* gvt = c->gvt.get(ddN);
+  double* vt = c->tmpA.get(dN);
+  double* G = c->w64.G.get(dN);
+  identity_tensor(F, d, N, c->s);
+  const int nF = c->n_t * substeps;
+  const double h = 1.0 / nF;
+  for (int j = 0; j < nF; ++j) {
+    for (int stage = 0; stage < 2; ++stage) {
+      double t = (double)(j + stage) * h;
+      const double* vv = v;
+      const double* gg = gvl;
+      if (nc > 1) {
+        Coefs b = basis_at(c, t);
+        vel_at<double, double>(v, nc, b, vt, dN, c->s);
+        vel_at<double, double>(gvl, nc, b, gvt, ddN, c->s);
+        vv = vt;
+        gg = gvt;
+      }
+      const double* Fin = stage ? Fh : F;
+      double* Kout = stage ? K2 : K1;
+      for (int q = 0; q < dd; ++q) {
+        grad_into<double>(c, Fin + q * N, G);
+        detF_rhs(G, vv, gg, Fin, q, Kout, d, N, c->s);
+      }
+      if (stage == 0) {
+        lincomb(1.0, F, h, K1, Fh, ddN, c->s);
+      } else {
+        axpby(0.5 * h, K1, 1.0, F, ddN, c->s);
+        axpby(0.5 * h, K2, 1.0, F, ddN, c->s);
+      }
+    }
+  }
+  double* det = det_out ? det_out : c->det.get(N);
+  det_tensor(F, det, d, N, c->s);
+  stats(det, N, red(c), c->s, st);
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1: inexact Gauss-Newton-Krylov with PCG (Nocedal & Wright Alg. 5.3),
+// forcing term Eq. termination-criterion-ksm, Armijo backtracking.
+// ---------------------------------------------------------------------------
+int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
+  auto t0 = std::chrono::steady_clock::now();
+  const long n = c->ncdN();
+  double* g = c->sv_g.get(n);
+  double* s = c->sv_s.get(n);
+  double* r = c->sv_r.get(n);
+  double* z = c->sv_z.get(n);
+  double* p = c->sv_p.get(n);
+  double* Hp = c->sv_Hp.get(n);
+  double* vt = c->sv_vt.get(n);
+  double* rs = red(c);
+  std::memset(&R, 0, sizeof(R));
+  double parts[2];
+  gradient(c, v, g, parts);
+  R.n_pde += 2;
+  double J = parts[0] + parts[1];
+  R.J0 = J;
+  R.g0_inf = maxabs(g, n, rs, c->s);
+  double g0_2 = std::sqrt(dot(g, g, n, rs, c->s));
+  long maxit = o.pcg_maxit > 0 ? o.pcg_maxit : n;
+  int status = REG_OK;
+  int k = 0;
+  for (;;) {
+    double ginf = maxabs(g, n, rs, c->s);
+    double g2 = std::sqrt(dot(g, g, n, rs, c->s));
+    R.g_inf = ginf;
+    R.J = J;
+    if (ginf <= o.grad_rtol * R.g0_inf) break;
+    if (k >= o.max_outer) {
+      status = REG_EMAXIT;
+      break;
+    }
+    double eta = std::min(0.5, std::sqrt(g2 / g0_2));
+    // PCG on H s = -g from s = 0
+    REG_CUDA(cudaMemsetAsync(s, 0, n * sizeof(double), c->s));
+    REG_CUDA(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    precond(c, r, z);
+    lincomb(-1.0, z, 0.0, z, p, n, c->s);
+    double rz = dot(r, z, n, rs, c->s);
+    for (long it = 0; it < maxit; ++it) {
+      double rn = std::sqrt(dot(r, r, n, rs, c->s));
+      check_finite(rn, "PCG residual");
+      if (rn <= eta * g2) break;
+      hessvec(c, p, Hp);
+      R.matvecs += 1;
+      R.n_pde += 2;
+      R.pcg_iters += 1;
+      double pHp = dot(p, Hp, n, rs, c->s);
+      check_finite(pHp, "PCG curvature");
+      if (pHp <= 0.0) {
+        if (it == 0) REG_CUDA(cudaMemcpyAsync(s, p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+        break;
+      }
+      double alpha = rz / pHp;
+      axpby(alpha, p, 1.0, s, n, c->s);
+      axpby(alpha, Hp, 1.0, r, n, c->s);
+      precond(c, r, z);
+      double rz_new = dot(r, z, n, rs, c->s);
+      double bta = rz_new / rz;
+      rz = rz_new;
+      axpby(-1.0, z, bta, p, n, c->s);
+    }
+    // keep the step inside the CFL bound by halving it (Sec. 3.3.5)
+    if (o.cfl_max > 0) {
+      int halvings = 0;
+      for (;;) {
+        lincomb(1.0, v, 1.0, s, vt, n, c->s);
+        if (cfl(c, vt) <= o.cfl_max) break;
+        if (++halvings > 30) throw StatusError{REG_ECFL, "CFL bound not met after 30 step halvings"};
+        axpby(0.0, s, 0.5, s, n, c->s);
+        R.cfl_halvings += 1;
+      }
+    }
+    // Armijo backtracking from alpha = 1
+    double slope = c->hd * dot(g, s, n, rs, c->s);
+    double alpha = 1.0, Jt = 0.0;
+    bool accepted = false;
+    for (int t = 0; t < o.max_backtracks; ++t) {
+      lincomb(1.0, v, alpha, s, vt, n, c->s);
+      double pt[2];
+      objective(c, vt, pt);
+      R.ls_trials += 1;
+      R.n_pde += 1;
+      Jt = pt[0] + pt[1];
+      if (std::isfinite(Jt) && Jt <= J + o.armijo_c1 * alpha * slope) {
+        accepted = true;
+        break;
+      }
+      alpha *= o.backtrack;
+    }
+    if (!accepted) {
+      status = REG_ELINESEARCH;
+      break;
+    }
+    REG_CUDA(cudaMemcpyAsync(v, vt, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    gradient(c, v, g, parts);
+    R.n_pde += 2;
+    J = parts[0] + parts[1];
+    k += 1;
+  }
+  R.outer = k;
+  R.J = J;
+  double base = sqdiff(c->mT.p, c->mR.p, c->N(), rs, c->s);
+  double pt[2];
+  objective(c, v, pt);
+  R.dist_rel = base > 0 ? (2.0 * pt[0] / c->hd) / base : 0.0;
+  R.cfl = cfl(c, v);
+  if (o.detF_substeps > 0) detF(c, v, o.detF_substeps, R.detF, nullptr);
+  REG_CUDA(cudaStreamSynchronize(c->s));
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  R.status = status;
+  return status;
+}
+
+reg_status fail(reg_ctx* c, int st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return (reg_status)st;
+}
+
+}  // namespace
+
+#define API_BEGIN(ctx)                                          \
+  if (!(ctx)) return fail(nullptr, REG_EINVAL, "null context"); \
+  reg_ctx* c_ = (ctx);                                          \
+  c_->err.clear();                                              \
+  tl_prof = c_->prof.mask ? &c_->prof : nullptr;                \
+  try {
+#define API_END                                                                                       \
+  }                                                                                                   \
+  catch (const StatusError& e) {                                                                      \
+    return fail(c_, e.status, e.what);                                                                \
+  }                                                                                                   \
+  catch (const CudaError& e) {                                                                        \
+    return fail(c_, e.code == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA, e.what);            \
+  }                                                                                                   \
+  catch (const std::bad_alloc&) {                                                                     \
+    return fail(c_, REG_ENOMEM, "host allocation failed");                                            \
+  }                                                                                                   \
+  return REG_OK;
+
+extern "C" {
+
+reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, int n_c, double beta, int reg_type, int stokes,
+                      int precision, int ckpt_every, void* cuda_stream) {
+  if (!out) return fail(nullptr, REG_EINVAL, "out is null");
+  *out = nullptr;
+  if (!n) return fail(nullptr, REG_EINVAL, "n is null");
+  if (n_t < 1) return fail(nullptr, REG_EINVAL, "n_t must be >= 1");
+  if (n_c < 1 || n_c > 16) return fail(nullptr, REG_EINVAL, "n_c must be in [1, 16]");
+  if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, REG_EINVAL, "beta must be positive and finite");
+  if (reg_type != REG_H1 && reg_type != REG_H2) return fail(nullptr, REG_EINVAL, "reg_type must be REG_H1 or REG_H2");
+  if (stokes != 0 && stokes != 1) return fail(nullptr, REG_EINVAL, "stokes must be 0 or 1");
+  if (precision != REG_FP64 && precision != REG_MIXED) return fail(nullptr, REG_EINVAL, "bad precision");
+  if (ckpt_every < 0 || (ckpt_every > 0 && n_t % ckpt_every != 0))
+    return fail(nullptr, REG_EINVAL, "ckpt_every must be 0 or divide n_t");
+  reg_ctx* c = nullptr;
+  try {
+    Grid g = make_grid(d, n);
+    c = new reg_ctx();
+    c->d = d;
+    c->g = g;
+    c->n_t = n_t;
+    c->n_c = n_c;
+    c->beta = beta;
+    c->rtype = reg_type;
+    c->stokes = stokes;
+    c->prec = precision;
+    c->ckpt = ckpt_every;
+    c->s = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < d; ++i) c->hd *= 2.0 * M_PI / g.n[i];
+    c->bnode.resize((size_t)(n_t + 1) * n_c);
+    for (int j = 0; j <= n_t; ++j) cheb_values(n_c, (double)j / n_t, &c->bnode[(size_t)j * n_c]);
+    c->Cg.resize(n_c * n_c);
+    for (int a = 0; a < n_c; ++a)
+      for (int b = 0; b < n_c; ++b) c->Cg[a * n_c + b] = cheb_gram_entry(a, b);
+    if (!invert_small(n_c, c->Cg, c->Ci)) throw StatusError{REG_EINVAL, "singular Gram matrix"};
+    REG_CUDA(cudaMemcpy(c->Cg_dev.get(n_c * n_c), c->Cg.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
+    REG_CUDA(cudaMemcpy(c->Ci_dev.get(n_c * n_c), c->Ci.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
+    c->sp64.reset(new Spectral<double>(g, c->s));
+    if (precision == REG_MIXED) c->sp32.reset(new Spectral<float>(g, c->s));
+  } catch (const StatusError& e) {
+    delete c;
+    return fail(nullptr, e.status, e.what);
+  } catch (const CudaError& e) {
+    delete c;
+    return fail(nullptr, e.code == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA, e.what);
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return fail(nullptr, REG_ENOMEM, "host allocation failed");
+  }
+  *out = c;
+  return REG_OK;
+}
+
+reg_status reg_destroy(reg_ctx* ctx) {
+  if (!ctx) return REG_OK;
+  cudaStreamSynchronize(ctx->s);
+  delete ctx;
+  return REG_OK;
+}
+
+const char* reg_last_error(const reg_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+reg_status reg_set_quadrature(reg_ctx* ctx, int quadrature) {
+  API_BEGIN(ctx)
+  if (quadrature != REG_QUAD_TRAPEZOID && quadrature != REG_QUAD_DISCRETE)
+    throw StatusError{REG_EINVAL, "bad quadrature"};
+  c_->quad = quadrature;
+  c_->ready = false;
+  API_END
+}
+
+reg_status reg_set_images(reg_ctx* ctx, const double* m_T, const double* m_R) {
+  API_BEGIN(ctx)
+  const long N = c_->N();
+  const double* a = input_ptr(c_, m_T, N, 0);
+  const double* b = input_ptr(c_, m_R, N, 1);
+  REG_CUDA(cudaMemcpyAsync(c_->mT.get(N), a, N * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+  REG_CUDA(cudaMemcpyAsync(c_->mR.get(N), b, N * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+  REG_CUDA(cudaStreamSynchronize(c_->s));
+  c_->have_images = true;
+  c_->ready = false;
+  API_END
+}
+
+reg_status reg_objective(reg_ctx* ctx, const double* v, double* J_out, double* parts) {
+  API_BEGIN(ctx)
+  if (!J_out) throw StatusError{REG_EINVAL, "J_out is null"};
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  double p[2];
+  objective(c_, vd, p);
+  check_finite(p[0] + p[1], "objective");
+  *J_out = p[0] + p[1];
+  if (parts) {
+    parts[0] = p[0];
+    parts[1] = p[1];
+  }
+  API_END
+}
+
+reg_status reg_gradient(reg_ctx* ctx, const double* v, double* g, double* J_out) {
+  API_BEGIN(ctx)
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  Output o(c_, g, c_->ncdN(), c_->stage_out);
+  double p[2];
+  gradient(c_, vd, o.dev, p);
+  o.finish();
+  if (J_out) *J_out = p[0] + p[1];
+  API_END
+}
+
+reg_status reg_linearize(reg_ctx* ctx, const double* v) {
+  API_BEGIN(ctx)
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  set_point(c_, vd);
+  prepare_mixed(c_);
+  REG_CUDA(cudaStreamSynchronize(c_->s));
+  c_->ready = true;
+  API_END
+}
+
+reg_status reg_hessvec(reg_ctx* ctx, const double* vt, double* Hvt) {
+  API_BEGIN(ctx)
+  const double* vd = input_ptr(c_, vt, c_->ncdN(), 0);
+  Output o(c_, Hvt, c_->ncdN(), c_->stage_out);
+  hessvec(c_, vd, o.dev);
+  o.finish();
+  API_END
+}
+
+reg_status reg_precond(reg_ctx* ctx, const double* r, double* z) {
+  API_BEGIN(ctx)
+  const double* rd = input_ptr(c_, r, c_->ncdN(), 0);
+  Output o(c_, z, c_->ncdN(), c_->stage_out);
+  precond(c_, rd, o.dev);
+  o.finish();
+  API_END
+}
+
+reg_status reg_regularization(reg_ctx* ctx, const double* v, double* out) {
+  API_BEGIN(ctx)
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  Output o(c_, out, c_->ncdN(), c_->stage_out);
+  tail(c_, vd, nullptr, o.dev);
+  o.finish();
+  API_END
+}
+
+reg_status reg_transport(reg_ctx* ctx, const double* v, const double* m0, double* m1) {
+  API_BEGIN(ctx)
+  const long N = c_->N();
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  const double* md = input_ptr(c_, m0, N, 1);
+  Output o(c_, m1, N, c_->stage_out);
+  Work<double>& w = c_->w64;
+  REG_CUDA(cudaMemcpyAsync(w.m.get(N), md, N * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+  state_steps<double>(c_, vd, 0, c_->n_t, nullptr, nullptr, 0, nullptr);
+  REG_CUDA(cudaMemcpyAsync(o.dev, w.m.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+  o.finish();
+  API_END
+}
+
+reg_status reg_transport_adjoint(reg_ctx* ctx, const double* v, const double* m0, const double* G, double* grad_v,
+                                 double* grad_m0) {
+  API_BEGIN(ctx)
+  const long N = c_->N();
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  const double* md = input_ptr(c_, m0, N, 1);
+  const double* Gd = input_ptr(c_, G, N, 2);
+  c_->ready = false;  // the stored state now belongs to (v, m0)
+  double* vc = c_->tmpA.get(c_->ncdN());
+  REG_CUDA(cudaMemcpyAsync(vc, vd, c_->ncdN() * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+  state_solve_store<double>(c_, vc, md);
+  Work<double>& w = c_->w64;
+  lincomb_t<double>(-1.0, Gd, 0.0, nullptr, w.lam.get(N), N, c_->s);  // lam_1 = -G
+  double* f = c_->f.get(c_->ncdN());
+  adjoint_solve<double>(c_, vc, f);
+  if (grad_v) {
+    Output o(c_, grad_v, c_->ncdN(), c_->stage_out);
+    REG_CUDA(cudaMemcpyAsync(o.dev, f, c_->ncdN() * sizeof(double), cudaMemcpyDeviceToDevice, c_->s));
+    o.finish();
+  }
+  if (grad_m0) {
+    Output o(c_, grad_m0, N, c_->stage_out);
+    lincomb_t<double>(-1.0, w.lam.p, 0.0, nullptr, o.dev, N, c_->s);
+    o.finish();
+  }
+  REG_CUDA(cudaStreamSynchronize(c_->s));
+  API_END
+}
+
+reg_status reg_detF(reg_ctx* ctx, const double* v, int substeps, double* stats_out, double* detF_out) {
+  API_BEGIN(ctx)
+  if (substeps < 1) throw StatusError{REG_EINVAL, "substeps must be >= 1"};
+  if (!stats_out) throw StatusError{REG_EINVAL, "stats is null"};
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  double st[4];
+  if (detF_out) {
+    Output o(c_, detF_out, c_->N(), c_->stage_out);
+    detF(c_, vd, substeps, st, o.dev);
+    o.finish();
+  } else {
+    detF(c_, vd, substeps, st, nullptr);
+  }
+  for (int i = 0; i < 4; ++i) stats_out[i] = st[i];
+  API_END
+}
+
+reg_status reg_cfl(reg_ctx* ctx, const double* v, double* cfl_out) {
+  API_BEGIN(ctx)
+  if (!cfl_out) throw StatusError{REG_EINVAL, "cfl_out is null"};
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  *cfl_out = cfl(c_, vd);
+  API_END
+}
+
+reg_status reg_profile_begin(reg_ctx* ctx, unsigned kind_mask) {
+  API_BEGIN(ctx)
+  double ms[KK_COUNT], by[KK_COUNT];
+  long cnt[KK_COUNT];
+  c_->prof.collect(ms, by, cnt);  // drop anything left over
+  c_->prof.mask = kind_mask;
+  API_END
+}
+
+reg_status reg_profile_end(reg_ctx* ctx, double* ms, double* bytes, long* count) {
+  API_BEGIN(ctx)
+  double m[KK_COUNT], b[KK_COUNT];
+  long n[KK_COUNT];
+  c_->prof.collect(m, b, n);
+  c_->prof.mask = 0;
+  for (int k = 0; k < KK_COUNT; ++k) {
+    if (ms) ms[k] = m[k];
+    if (bytes) bytes[k] = b[k];
+    if (count) count[k] = n[k];
+  }
+  API_END
+}
+
+long reg_launch_count(void) { return launch_count(); }
+
+void reg_solve_opts_default(reg_solve_opts* o) {
+  if (!o) return;
+  o->grad_rtol = 1e-2;
+  o->max_outer = 50;
+  o->armijo_c1 = 1e-4;
+  o->backtrack = 0.5;
+  o->max_backtracks = 20;
+  o->pcg_maxit = 0;
+  o->cfl_max = 0.0;
+  o->detF_substeps = 0;
+}
+
+reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report) {
+  API_BEGIN(ctx)
+  reg_solve_opts o;
+  reg_solve_opts_default(&o);
+  if (opts) o = *opts;
+  if (!v_inout) throw StatusError{REG_EINVAL, "v_inout is null"};
+  Output io(c_, v_inout, c_->ncdN(), c_->stage_out);
+  if (io.host)
+    REG_CUDA(cudaMemcpyAsync(io.dev, v_inout, c_->ncdN() * sizeof(double), cudaMemcpyHostToDevice, c_->s));
+  reg_solve_report R;
+  int st = solve(c_, io.dev, o, R);
+  io.finish();
+  if (report) *report = R;
+  if (st != REG_OK) throw StatusError{st, st == REG_EMAXIT ? "outer iteration cap reached" : "line search failed"};
+  API_END
+}
+
+}  // extern "C"

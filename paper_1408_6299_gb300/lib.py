@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the CUDA registration library (``include/reg.h``).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels. Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they must
+be float64 and contiguous. There is no CPU fallback: if the library cannot be
+built or loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+REG_OK, REG_EINVAL, REG_ENOMEM, REG_ECUDA, REG_ENOTREADY = 0, 1, 2, 3, 4
+REG_ENONFINITE, REG_ECFL, REG_ELINESEARCH, REG_EMAXIT, REG_ETIMEOUT = 5, 6, 7, 8, 9
+REG_H1, REG_H2 = 1, 2
+REG_FP64, REG_MIXED = 0, 1
+REG_QUAD_TRAPEZOID, REG_QUAD_DISCRETE = 0, 1
+
+_STATUS = {0: "REG_OK", 1: "REG_EINVAL", 2: "REG_ENOMEM", 3: "REG_ECUDA", 4: "REG_ENOTREADY",
+           5: "REG_ENONFINITE", 6: "REG_ECFL", 7: "REG_ELINESEARCH", 8: "REG_EMAXIT", 9: "REG_ETIMEOUT"}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [
+        ("grad_rtol", ctypes.c_double),
+        ("max_outer", ctypes.c_int),
+        ("armijo_c1", ctypes.c_double),
+        ("backtrack", ctypes.c_double),
+        ("max_backtracks", ctypes.c_int),
+        ("pcg_maxit", ctypes.c_long),
+        ("cfl_max", ctypes.c_double),
+        ("detF_substeps", ctypes.c_int),
+    ]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [
+        ("outer", ctypes.c_int),
+        ("pcg_iters", ctypes.c_long),
+        ("matvecs", ctypes.c_long),
+        ("n_pde", ctypes.c_long),
+        ("ls_trials", ctypes.c_int),
+        ("cfl_halvings", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("J0", ctypes.c_double),
+        ("J", ctypes.c_double),
+        ("g0_inf", ctypes.c_double),
+        ("g_inf", ctypes.c_double),
+        ("dist_rel", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("detF", ctypes.c_double * 4),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            val = getattr(self, name)
+            out[name] = list(val) if name == "detF" else val
+        return out
+
+
+class RegError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_SIGNATURES = {
+    "reg_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "reg_destroy": [_vp],
+    "reg_set_quadrature": [_vp, ctypes.c_int],
+    "reg_set_images": [_vp, _vp, _vp],
+    "reg_objective": [_vp, _vp, _vp, _vp],
+    "reg_gradient": [_vp, _vp, _vp, _vp],
+    "reg_linearize": [_vp, _vp],
+    "reg_hessvec": [_vp, _vp, _vp],
+    "reg_precond": [_vp, _vp, _vp],
+    "reg_regularization": [_vp, _vp, _vp],
+    "reg_transport": [_vp, _vp, _vp, _vp],
+    "reg_transport_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "reg_detF": [_vp, _vp, ctypes.c_int, _vp, _vp],
+    "reg_cfl": [_vp, _vp, _vp],
+    "reg_solve": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
+    "reg_profile_begin": [_vp, ctypes.c_uint],
+    "reg_profile_end": [_vp, _vp, _vp, _vp],
+}
+
+EXPORTED = tuple(_SIGNATURES) + ("reg_last_error", "reg_solve_opts_default", "reg_launch_count")
+KIND_NAMES = ("rows_r2c", "rows_c2r", "cols", "mult", "stage", "force", "other")
+
+
+def launch_count():
+    return int(load().reg_launch_count())
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load (building first if needed) the CUDA library; raise if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"registration CUDA library missing at {path}")
+            L = ctypes.CDLL(path)
+            for name, args in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.reg_last_error.argtypes = [_vp]
+            L.reg_last_error.restype = ctypes.c_char_p
+            L.reg_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+            L.reg_solve_opts_default.restype = None
+            L.reg_launch_count.argtypes = []
+            L.reg_launch_count.restype = ctypes.c_long
+            _lib = L
+    return _lib
+
+
+def _addr(a):
+    """(address, keepalive) of a contiguous float64 torch tensor or numpy array."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise TypeError("tensors passed to the registration library must be contiguous float64")
+            return a.data_ptr(), a
+    except ImportError:
+        pass
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("arrays passed to the registration library must be C-contiguous float64")
+        return a.ctypes.data, a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Registration:
+    """One library context: grid, time discretisation and regulariser fixed at creation."""
+
+    def __init__(self, n, n_t, n_c=1, beta=1e-2, reg=REG_H1, stokes=False, precision=REG_FP64, ckpt_every=0,
+                 stream=None, quadrature=REG_QUAD_TRAPEZOID):
+        self.L = load()
+        self.n = tuple(int(k) for k in n)
+        self.d = len(self.n)
+        self.n_t, self.n_c = int(n_t), int(n_c)
+        ctx = _vp()
+        arr = (ctypes.c_int64 * self.d)(*self.n)
+        st = self.L.reg_create(ctypes.byref(ctx), self.d, arr, self.n_t, self.n_c, float(beta), int(reg),
+                               int(bool(stokes)), int(precision), int(ckpt_every), stream)
+        if st != REG_OK:
+            raise RegError(st, self.L.reg_last_error(None).decode())
+        self.ctx = ctx
+        if quadrature != REG_QUAD_TRAPEZOID:
+            self._check(self.L.reg_set_quadrature(self.ctx, int(quadrature)))
+
+    @property
+    def N(self):
+        return int(np.prod(self.n))
+
+    def coef_shape(self):
+        return (self.n_c, self.d) + self.n
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.L.reg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != REG_OK:
+            raise RegError(st, self.L.reg_last_error(self.ctx).decode())
+
+    # each method passes raw pointers through; outputs are caller-allocated
+    def set_images(self, mT, mR):
+        a, ka = _addr(mT)
+        b, kb = _addr(mR)
+        self._check(self.L.reg_set_images(self.ctx, a, b))
+
+    def objective(self, v):
+        a, ka = _addr(v)
+        J = ctypes.c_double()
+        parts = (ctypes.c_double * 2)()
+        self._check(self.L.reg_objective(self.ctx, a, ctypes.byref(J), parts))
+        return J.value, (parts[0], parts[1])
+
+    def gradient(self, v, g):
+        a, ka = _addr(v)
+        b, kb = _addr(g)
+        J = ctypes.c_double()
+        self._check(self.L.reg_gradient(self.ctx, a, b, ctypes.byref(J)))
+        return J.value
+
+    def linearize(self, v):
+        a, ka = _addr(v)
+        self._check(self.L.reg_linearize(self.ctx, a))
+
+    def hessvec(self, vt, out):
+        a, ka = _addr(vt)
+        b, kb = _addr(out)
+        self._check(self.L.reg_hessvec(self.ctx, a, b))
+
+    def precond(self, r, z):
+        a, ka = _addr(r)
+        b, kb = _addr(z)
+        self._check(self.L.reg_precond(self.ctx, a, b))
+
+    def regularization(self, v, out):
+        a, ka = _addr(v)
+        b, kb = _addr(out)
+        self._check(self.L.reg_regularization(self.ctx, a, b))
+
+    def transport(self, v, m0, m1):
+        a, ka = _addr(v)
+        b, kb = _addr(m0)
+        c, kc = _addr(m1)
+        self._check(self.L.reg_transport(self.ctx, a, b, c))
+
+    def transport_adjoint(self, v, m0, G, grad_v=None, grad_m0=None):
+        a, ka = _addr(v)
+        b, kb = _addr(m0)
+        c, kc = _addr(G)
+        d, kd = _addr(grad_v)
+        e, ke = _addr(grad_m0)
+        self._check(self.L.reg_transport_adjoint(self.ctx, a, b, c, d, e))
+
+    def detF(self, v, substeps=1, out=None):
+        a, ka = _addr(v)
+        b, kb = _addr(out)
+        st = (ctypes.c_double * 4)()
+        self._check(self.L.reg_detF(self.ctx, a, int(substeps), st, b))
+        return tuple(st)
+
+    def cfl(self, v):
+        a, ka = _addr(v)
+        c = ctypes.c_double()
+        self._check(self.L.reg_cfl(self.ctx, a, ctypes.byref(c)))
+        return c.value
+
+    def profile_begin(self, mask=(1 << 7) - 1):
+        self._check(self.L.reg_profile_begin(self.ctx, int(mask)))
+
+    def profile_end(self):
+        ms = (ctypes.c_double * 7)()
+        by = (ctypes.c_double * 7)()
+        cnt = (ctypes.c_long * 7)()
+        self._check(self.L.reg_profile_end(self.ctx, ms, by, cnt))
+        return {KIND_NAMES[k]: dict(ms=ms[k], bytes=by[k], launches=cnt[k]) for k in range(7)}
+
+    def solve(self, v, **opts):
+        """Solve in place on v; returns the report dict (raises on a failed solve)."""
+        o = SolveOpts()
+        self.L.reg_solve_opts_default(ctypes.byref(o))
+        for k, val in opts.items():
+            setattr(o, k, val)
+        a, ka = _addr(v)
+        rep = SolveReport()
+        st = self.L.reg_solve(self.ctx, a, ctypes.byref(o), ctypes.byref(rep))
+        out = rep.as_dict()
+        out["status"] = st
+        if st not in (REG_OK, REG_EMAXIT):
+            self._check(st)
+        return out

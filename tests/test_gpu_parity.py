@@ -1,0 +1,194 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs are seeded synthetic workloads (paper_1408_6299_gb300.synth); the
+reference image is the template transported by the true velocity with the
+oracle's own solver, and both sides take that same m_R. Tolerances: FP64 path
+relative 1e-10, mixed-precision Hessian matvec relative 1e-5 (per result,
+relative 2-norm over the whole coefficient vector, plus an elementwise bound
+against the largest entry).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1408_6299_gb300 import lib, synth
+from gpu_util import cuda, empty, host, pair, rel, relmax
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-5
+
+
+def small_cases():
+    # (workload, label): grids chosen to cover 2D/3D, non-square shapes, several
+    # FFT tiles per axis, partial row blocks, n_c > 1 and the Stokes scheme
+    return [
+        (synth.sinusoid_2d(32), "sin32"),
+        (dict(synth.blobs_2d(64, n_t=8), n=(64, 64)), "blobs64"),
+        (synth.stokes_3d(16, n_t=6, n_c=3), "stokes16"),
+    ]
+
+
+def nonsquare_case():
+    r = np.random.default_rng(77)
+    n = (8, 32, 16)
+    mT = synth.random_spectral_field(n, r, 6.0)
+    v = np.stack([synth.velocity_field(n, r, 3, 0.3)])
+    vt = np.stack([synth.velocity_field(n, r, 3, 1.0)])
+    return dict(name="nonsquare", n=n, n_t=4, n_c=1, beta=2e-2, reg=2, stokes=False, mT=mT, v_true=v, vt=vt)
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = small_cases() + [(nonsquare_case(), "nonsq")]
+    for c, _ in out:
+        P = O.Problem(c["n"], c["n_t"], c["n_c"], c["beta"], c["reg"], c["stokes"])
+        c["mR"] = P.state(c["v_true"], c["mT"])[-1]
+    return out
+
+
+def test_spectral_operators(cases):
+    for c, label in cases:
+        R, P = pair(c)
+        r = np.random.default_rng(5).standard_normal(R.coef_shape())
+        out = empty(R.coef_shape())
+        R.regularization(cuda(r), out)
+        assert rel(host(out), P.reg_apply(r)) < 1e-12, label
+        R.precond(cuda(r), out)
+        assert rel(host(out), P.precond(r)) < 1e-12, label
+
+
+def test_transport_and_objective(cases):
+    for c, label in cases:
+        R, P = pair(c)
+        m1 = empty(c["n"])
+        R.transport(cuda(c["v_true"]), cuda(c["mT"]), m1)
+        ref = P.state(c["v_true"], c["mT"])[-1]
+        assert rel(host(m1), ref) < FP64_TOL, label
+        R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+        v = 0.5 * c["v_true"]
+        J, parts = R.objective(cuda(v))
+        Jo, do, ro = P.objective(v, c["mT"], c["mR"])
+        assert abs(J - Jo) < FP64_TOL * Jo, label
+        assert abs(parts[0] - do) < FP64_TOL * Jo and abs(parts[1] - ro) < FP64_TOL * Jo, label
+
+
+@pytest.mark.parametrize("quad", [0, 1])
+def test_gradient_fp64(cases, quad):
+    for c, label in cases:
+        R, P = pair(c, quad=quad)
+        R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+        v = 0.5 * c["v_true"]
+        g = empty(R.coef_shape())
+        J = R.gradient(cuda(v), g)
+        go, Jo = P.gradient(v, c["mT"], c["mR"])
+        assert rel(host(g), go) < FP64_TOL, (label, rel(host(g), go))
+        assert relmax(host(g), go) < 10 * FP64_TOL, label
+        assert abs(J - Jo) < FP64_TOL * Jo, label
+
+
+@pytest.mark.parametrize("precision,ckpt,quad", [
+    (lib.REG_FP64, 0, 0), (lib.REG_FP64, 2, 0), (lib.REG_FP64, 0, 1), (lib.REG_FP64, 2, 1),
+    (lib.REG_MIXED, 0, 0), (lib.REG_MIXED, 2, 0), (lib.REG_MIXED, 0, 1)])
+def test_hessvec(cases, precision, ckpt, quad):
+    tol = FP64_TOL if precision == lib.REG_FP64 else MIXED_TOL
+    for c, label in cases:
+        R, P = pair(c, precision=precision, ckpt=ckpt, quad=quad)
+        R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+        v = c["v_true"]
+        R.linearize(cuda(v))
+        Hv = empty(R.coef_shape())
+        R.hessvec(cuda(c["vt"]), Hv)
+        ref = P.hessvec(v, c["mT"], c["vt"])
+        err = rel(host(Hv), ref)
+        assert err < tol, (label, err)
+        assert relmax(host(Hv), ref) < 10 * tol, label
+
+
+def test_hessvec_host_buffers_and_aliasing(cases):
+    c, label = cases[0]
+    R, P = pair(c)
+    R.set_images(c["mT"], c["mR"])  # host numpy arrays: staged by the library
+    R.linearize(c["v_true"])
+    buf = np.ascontiguousarray(c["vt"], dtype=np.float64).copy()
+    R.hessvec(buf, buf)  # aliasing input and output
+    ref = P.hessvec(c["v_true"], c["mT"], c["vt"])
+    assert rel(buf, ref) < FP64_TOL
+
+
+def test_hessvec_before_point_is_rejected(cases):
+    c, _ = cases[0]
+    R, _ = pair(c)
+    R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+    with pytest.raises(lib.RegError) as e:
+        R.hessvec(cuda(c["vt"]), empty(R.coef_shape()))
+    assert e.value.status == lib.REG_ENOTREADY
+
+
+def test_transport_adjoint(cases):
+    for c, label in cases:
+        R, P = pair(c, quad=1)
+        G = np.random.default_rng(3).standard_normal(c["n"])
+        gv, gm0 = empty(R.coef_shape()), empty(c["n"])
+        R.transport_adjoint(cuda(c["v_true"]), cuda(c["mT"]), cuda(G), gv, gm0)
+        # oracle: with m_R = m_1 + G the adjoint starts from lambda_1 = -G
+        Pn = O.Problem(c["n"], c["n_t"], c["n_c"], c["beta"], c["reg"], False, dto=True)
+        m1 = Pn.state(c["v_true"], c["mT"])[-1]
+        g, _ = Pn.gradient(c["v_true"], c["mT"], m1 - G)
+        f = g - Pn.reg_apply(c["v_true"])
+        assert rel(host(gv), f) < FP64_TOL, label
+        lam0 = Pn.adjoint(c["v_true"], -G)[0]
+        assert rel(host(gm0), -lam0) < FP64_TOL, label
+
+
+def test_detF_and_cfl(cases):
+    for c, label in cases:
+        R, P = pair(c)
+        det = empty(c["n"])
+        st = R.detF(cuda(c["v_true"]), 1, det)
+        ref = P.detF(c["v_true"])
+        assert relmax(host(det), ref) < 1e-12, label
+        assert abs(st[0] - ref.min()) < 1e-12 and abs(st[1] - ref.max()) < 1e-12
+        assert abs(st[2] - ref.mean()) < 1e-12 and abs(st[3] - ref.std()) < 1e-10
+        assert abs(R.cfl(cuda(c["v_true"])) - P.cfl(c["v_true"])) < 1e-13
+
+
+def test_solve_matches_oracle():
+    c = synth.sinusoid_2d()
+    R, P = pair(c)
+    c["mR"] = P.state(c["v_true"], c["mT"])[-1]
+    R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+    v = cuda(np.zeros(R.coef_shape()))
+    rep = R.solve(v, grad_rtol=1e-2, detF_substeps=4)
+    vo, repo = P.solve(c["mT"], c["mR"], grad_rtol=1e-2)
+    assert rep["status"] == 0 and repo["status"] == 0
+    assert rep["outer"] == repo["outer"] and rep["pcg_iters"] == repo["pcg_iters"]
+    assert rep["ls_trials"] == repo["ls_trials"]
+    assert rel(host(v), vo) < 1e-8
+    assert abs(rep["J"] - repo["J"]) < 1e-8 * repo["J"]
+    assert rep["g_inf"] <= 1e-2 * rep["g0_inf"]
+
+
+def test_mixed_solve_reaches_tolerance():
+    c = synth.blobs_2d(128)
+    R, P = pair(c, precision=lib.REG_MIXED)
+    c["mR"] = P.state(c["v_true"], c["mT"])[-1]
+    R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+    v = cuda(np.zeros(R.coef_shape()))
+    rep = R.solve(v, grad_rtol=1e-2)
+    assert rep["status"] == 0
+    assert rep["g_inf"] <= 1e-2 * rep["g0_inf"]
+    vo, repo = P.solve(c["mT"], c["mR"], grad_rtol=1e-2)
+    assert abs(rep["outer"] - repo["outer"]) <= 1
+    assert rel(host(v), vo) < 1e-3
+
+
+def test_bad_arguments_are_rejected():
+    with pytest.raises(lib.RegError) as e:
+        lib.Registration((12, 16), 4)
+    assert e.value.status == lib.REG_EINVAL
+    with pytest.raises(lib.RegError):
+        lib.Registration((16, 16), 6, ckpt_every=4)
+    with pytest.raises(lib.RegError):
+        lib.Registration((16, 16), 4, beta=-1.0)
