@@ -90,7 +90,8 @@ REG_API reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, i
 REG_API reg_status reg_destroy(reg_ctx* ctx);
 
 /* Text of the last error of ctx (never NULL; "" when none). Valid until the
- * next call on ctx. ctx may be NULL (then describes the last failed create). */
+ * next call on ctx. ctx may be NULL: then it describes the last failed
+ * reg_create or reg_precond_noalloc call of this thread. */
 REG_API const char* reg_last_error(const reg_ctx* ctx);
 
 /* Choose the time quadrature of the body force (default trapezoid). */
@@ -131,6 +132,30 @@ REG_API reg_status reg_hessvec(reg_ctx* ctx, const double* vt, double* Hvt);
  * a Fourier-diagonal scaling by 1/(beta a(k)) with the k = 0 mode scaled by
  * one, and the inverse Chebyshev Gram matrix across coefficients. */
 REG_API reg_status reg_precond(reg_ctx* ctx, const double* r, double* z);
+
+/* The preconditioner of reg_precond without a context and without allocating.
+ * The paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc when they need the operator (a runtime that owns all device
+ * memory through its own pool, a memory budget fixed at start-up, loops that
+ * must not allocate after initialisation). It computes the same z = P^{-1} r
+ * as reg_precond for the grid n[0..d-1], n_c, beta and reg_type, working in a
+ * fixed 64 MiB device array that every GPU loading this library reserves
+ * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   r, z: device pointers, n_c*d*N doubles each (z may equal r).
+ *   Limit: n_c*d*N/2 <= 2,095,040 (for example 3D 64^3 with n_c <= 3, 2D
+ *   512^2 with n_c <= 7); larger problems get REG_EINVAL and a message in
+ *   reg_last_error(NULL).
+ *   The first call on a device does a set-up with that device current: it
+ *   finds the array's address and uploads the FFT twiddle tables with a
+ *   synchronous host-to-device copy, so make that first call before any
+ *   stream capture. Later calls only enqueue kernels on cuda_stream (NULL =
+ *   legacy default stream) and return without synchronising.
+ *   Every call shares the array and it keeps the last call's contents; each
+ *   call overwrites all it reads. Calls whose GPU work overlaps (different
+ *   streams or host threads with no ordering between them) race on it. */
+REG_API reg_status reg_precond_noalloc(int d, const int64_t* n, int n_c, double beta, int reg_type, const double* r,
+                                       double* z, void* cuda_stream);
 
 /* Regularisation operator out = beta (C (x) A) v (App. A). */
 REG_API reg_status reg_regularization(reg_ctx* ctx, const double* v, double* out);

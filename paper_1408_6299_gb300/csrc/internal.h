@@ -91,13 +91,24 @@ struct Grid {
 
 Grid make_grid(int d, const int64_t* n);
 
+// set the text that reg_last_error(NULL) returns on this thread
+void set_thread_error(const std::string& msg);
+
 // Batched power-of-two FFTs and Fourier multipliers on one grid, in precision T.
 template <typename T>
 class Spectral {
  public:
   using C = cx<T>;
   Spectral(const Grid& g, cudaStream_t s);
+  // Non-owning engine over device tables laid out as write_tables() lays out
+  // its host image; allocates and copies nothing.
+  Spectral(const Grid& g, cudaStream_t s, C* tables, const long* tw_off, long rc_off);
   ~Spectral();
+  // Host image of the twiddle tables of every FFT length 4..512 followed by
+  // the real-to-complex tables of every last-axis length 8..512 (double,
+  // interleaved re/im). tw_off[e] / rc_off[e]: complex offset of the tables of
+  // length 2^e. out may be null to query the size; returns complex entries.
+  static long write_tables(double* out, long* tw_off, long* rc_off);
   Spectral(const Spectral&) = delete;
   Spectral& operator=(const Spectral&) = delete;
 
@@ -127,6 +138,7 @@ class Spectral {
   Grid g_;
   cudaStream_t s_;
   C* tw_ = nullptr;  // device: tables per length + real/complex table
+  bool owns_ = true;
   long tw_off_[11] = {0};  // offset of the table of length 2^e
   long rc_off_ = 0;
 };

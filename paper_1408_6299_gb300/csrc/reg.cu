@@ -685,6 +685,12 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
   return status;
 }
 
+}  // namespace
+
+void reg::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 reg_status fail(reg_ctx* c, int st, const std::string& msg) {
   if (c) c->err = msg;
   else g_create_error = msg;

@@ -470,8 +470,57 @@ Spectral<T>::Spectral(const Grid& g, cudaStream_t s) : g_(g), s_(s) {
 }
 
 template <typename T>
+Spectral<T>::Spectral(const Grid& g, cudaStream_t s, C* tables, const long* tw_off, long rc_off)
+    : g_(g), s_(s), tw_(tables), owns_(false) {
+  for (int e = 0; e < 11; ++e) tw_off_[e] = tw_off[e];
+  rc_off_ = rc_off;
+}
+
+template <typename T>
+long Spectral<T>::write_tables(double* out, long* tw_off, long* rc_off) {
+  long pos = 0;
+  auto put = [&](double re, double im) {
+    if (out) {
+      out[2 * pos] = re;
+      out[2 * pos + 1] = im;
+    }
+    ++pos;
+  };
+  for (int e = 0; e < 11; ++e) tw_off[e] = rc_off[e] = 0;
+  for (int e = 2; e <= 9; ++e) {
+    int L = 1 << e;
+    tw_off[e] = pos;
+    // the radix plan of Plan<L> (fft.cuh), in a fixed array: no heap use here
+    int R[3] = {L, 1, 1}, S = 1;
+    if (L == 32) { R[0] = 8; R[1] = 4; S = 2; }
+    else if (L == 64) { R[0] = 8; R[1] = 8; S = 2; }
+    else if (L == 128) { R[0] = 16; R[1] = 8; S = 2; }
+    else if (L == 256) { R[0] = 16; R[1] = 16; S = 2; }
+    else if (L == 512) { R[0] = 8; R[1] = 8; R[2] = 8; S = 3; }
+    int ns = R[0];
+    for (int st = 1; st < S; ++st) {
+      for (int r = 0; r < R[st]; ++r)
+        for (int k = 0; k < ns; ++k) {
+          double ang = -2.0 * M_PI * (double)(r * k) / (double)(ns * R[st]);
+          put(cos(ang), sin(ang));
+        }
+      ns *= R[st];
+    }
+  }
+  for (int e = 3; e <= 9; ++e) {
+    int L = 1 << e;
+    rc_off[e] = pos;
+    for (int k = 0; k < L / 2; ++k) {
+      double ang = -2.0 * M_PI * (double)k / (double)L;
+      put(cos(ang), sin(ang));
+    }
+  }
+  return pos;
+}
+
+template <typename T>
 Spectral<T>::~Spectral() {
-  if (tw_) cudaFree(tw_);
+  if (tw_ && owns_) cudaFree(tw_);
 }
 
 template <typename T>

@@ -92,6 +92,8 @@ _SIGNATURES = {
     "reg_detF": [_vp, _vp, ctypes.c_int, _vp, _vp],
     "reg_cfl": [_vp, _vp, _vp],
     "reg_solve": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
+    "reg_precond_noalloc": [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                            _vp, _vp, _vp],
     "reg_profile_begin": [_vp, ctypes.c_uint],
     "reg_profile_end": [_vp, _vp, _vp, _vp],
 }
@@ -102,6 +104,20 @@ KIND_NAMES = ("rows_r2c", "rows_c2r", "cols", "mult", "stage", "force", "other")
 
 def launch_count():
     return int(load().reg_launch_count())
+
+
+def precond_noalloc(n, n_c, beta, reg, r, z, stream=None):
+    """z = P^{-1} r like Registration.precond, without a context and without
+    allocating (fixed device scratch; r and z must be CUDA tensors). Returns
+    once the work is enqueued on `stream`."""
+    L = load()
+    n = tuple(int(k) for k in n)
+    arr = (ctypes.c_int64 * len(n))(*n)
+    a, ka = _addr(r)
+    b, kb = _addr(z)
+    st = L.reg_precond_noalloc(len(n), arr, int(n_c), float(beta), int(reg), a, b, stream)
+    if st != REG_OK:
+        raise RegError(st, L.reg_last_error(None).decode())
 
 
 def library_path():
