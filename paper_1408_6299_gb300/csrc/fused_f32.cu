@@ -1,0 +1,15 @@
+// fused_f32.cu -- single precision instantiation of the fused transport stages.
+#include "fused_launch.cuh"
+
+namespace reg {
+template <>
+void adv_stage<float>(Spectral<float>& sp, const float* u, const fused::AdvEpi<float>& e, float2* U, float2* Zx,
+                      float2* Zy) {
+  fused::adv_stage_impl<float>(sp, u, e, U, Zx, Zy);
+}
+template <>
+void div_stage<float>(Spectral<float>& sp, const float* lam, const float* a, const fused::DivEpi<float>& e,
+                      float2* Q0, float2* Q1, float2* Q2) {
+  fused::div_stage_impl<float>(sp, lam, a, e, Q0, Q1, Q2);
+}
+}  // namespace reg

@@ -1,0 +1,163 @@
+// fused_launch.cuh -- host launchers of the fused transport stages
+// (fused.cuh), instantiated once per precision by fused_f32.cu / fused_f64.cu.
+#pragma once
+#include "fused.cuh"
+
+namespace reg {
+namespace fused {
+
+constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : (n <= 2 ? 2 : 4); }
+
+// complex values per block of the row passes
+template <typename T>
+constexpr int row_elems() {
+  return sizeof(T) == 4 ? 4096 : 2048;
+}
+
+template <typename T, int L, int NF, bool PROD>
+void r2c_L(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out, int zmask,
+           const cx<T>* tw, const cx<T>* twrc) {
+  constexpr int M = L / 2;
+  constexpr int RB0 = row_elems<T>() / (pow2_ceil(NF) * M);
+  constexpr int RB = RB0 < 1 ? 1 : RB0;
+  ProfScope ps(KK_ROWS_R2C, s, (double)g.N * sizeof(T) * (2 * NF + (PROD ? 1 : 0)));
+  dim3 grid((unsigned)((g.rows + RB - 1) / RB));
+  k_rows_r2c_n<T, L, RB, NF, PROD><<<grid, kThreads, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
+  REG_LAUNCH();
+}
+
+template <typename T, int NF, bool PROD>
+void r2c(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out, int zmask,
+         const cx<T>* tw, const cx<T>* twrc) {
+  switch (g.L) {
+    case 8: return r2c_L<T, 8, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 16: return r2c_L<T, 16, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 32: return r2c_L<T, 32, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 64: return r2c_L<T, 64, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 128: return r2c_L<T, 128, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 256: return r2c_L<T, 256, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+    case 512: return r2c_L<T, 512, NF, PROD>(g, s, in, lam, out, zmask, tw, twrc);
+  }
+  throw StatusError{1, "unsupported last-axis length"};
+}
+
+template <typename T, int L, int NF, int EPI>
+void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
+           const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc) {
+  constexpr int M = L / 2;
+  constexpr int RB0 = row_elems<T>() / (pow2_ceil(NF) * M);
+  constexpr int RB = RB0 < 1 ? 1 : RB0;
+  ProfScope ps(KK_ROWS_C2R, s, bytes);
+  dim3 grid((unsigned)((g.rows + RB - 1) / RB));
+  k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc);
+  REG_LAUNCH();
+}
+
+template <typename T, int NF, int EPI>
+void c2r(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
+         const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc) {
+  switch (g.L) {
+    case 8: return c2r_L<T, 8, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 16: return c2r_L<T, 16, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 32: return c2r_L<T, 32, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 64: return c2r_L<T, 64, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 128: return c2r_L<T, 128, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 256: return c2r_L<T, 256, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 512: return c2r_L<T, 512, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+  }
+  throw StatusError{1, "unsupported last-axis length"};
+}
+
+template <typename T, int L, int TC>
+void deriv_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
+                  cudaStream_t st) {
+  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0));
+  dim3 grid((unsigned)(s / TC), (unsigned)outer);
+  k_cols_deriv<T, L, TC><<<grid, kThreads, 0, st>>>(in, out, add, s, tw);
+  REG_LAUNCH();
+}
+
+template <typename T, int L>
+void deriv_tc(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw, cudaStream_t st) {
+  constexpr int TCmax0 = sizeof(T) == 4 ? 16 : 8;
+  constexpr int TCmax = (L * TCmax0 * sizeof(cx<T>) > 32768) ? TCmax0 / 2 : TCmax0;
+  if (s >= TCmax) return deriv_launch<T, L, TCmax>(in, out, add, s, outer, tw, st);
+  if (s >= 4) return deriv_launch<T, L, 4>(in, out, add, s, outer, tw, st);
+  return deriv_launch<T, L, 2>(in, out, add, s, outer, tw, st);
+}
+
+// derivative along strided axis `axis` of the z-spectral rows
+template <typename T>
+void deriv(const Grid& g, const Spectral<T>& sp, int axis, const cx<T>* in, cx<T>* out, const cx<T>* add,
+           cudaStream_t st) {
+  long s = g.M;
+  for (int a = axis + 1; a < g.d - 1; ++a) s *= g.n[a];
+  long outer = g.Nc / (s * g.n[axis]);
+  const cx<T>* tw = sp.twiddles(g.n[axis]);
+  switch (g.n[axis]) {
+    case 8: return deriv_tc<T, 8>(in, out, add, s, outer, tw, st);
+    case 16: return deriv_tc<T, 16>(in, out, add, s, outer, tw, st);
+    case 32: return deriv_tc<T, 32>(in, out, add, s, outer, tw, st);
+    case 64: return deriv_tc<T, 64>(in, out, add, s, outer, tw, st);
+    case 128: return deriv_tc<T, 128>(in, out, add, s, outer, tw, st);
+    case 256: return deriv_tc<T, 256>(in, out, add, s, outer, tw, st);
+    case 512: return deriv_tc<T, 512>(in, out, add, s, outer, tw, st);
+  }
+  throw StatusError{1, "unsupported axis length"};
+}
+
+template <typename T>
+void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy) {
+  const Grid& g = sp.grid();
+  cudaStream_t s = sp.stream();
+  const cx<T>* tw = sp.twiddles(g.M);
+  const cx<T>* twrc = sp.rc_twiddles();
+  RowsIn<T, 1> in1{{u}};
+  RowsOut<T, 1> out1{{U}};
+  r2c<T, 1, false>(g, s, in1, nullptr, out1, 0, tw, twrc);
+  const int d = g.d;
+  double bytes = (double)g.N * sizeof(T) *
+                 (2 * d + (e.gm[0] ? 2 * d : 0) + (e.G[0] ? d : 0) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1));
+  DivEpi<T> none{};
+  if (d == 3) {
+    deriv<T>(g, sp, 1, U, Zy, nullptr, s);
+    deriv<T>(g, sp, 0, U, Zx, nullptr, s);
+    RowsSpec<T, 3> in{{Zx, Zy, U}};
+    c2r<T, 3, EPI_ADV>(g, s, in, 1 << 2, e, none, bytes, tw, twrc);
+  } else {
+    deriv<T>(g, sp, 0, U, Zy, nullptr, s);
+    RowsSpec<T, 2> in{{Zy, U}};
+    c2r<T, 2, EPI_ADV>(g, s, in, 1 << 1, e, none, bytes, tw, twrc);
+  }
+}
+
+template <typename T>
+void div_stage_impl(Spectral<T>& sp, const T* lam, const T* a, const DivEpi<T>& e, cx<T>* Q0, cx<T>* Q1,
+                    cx<T>* Q2) {
+  const Grid& g = sp.grid();
+  cudaStream_t s = sp.stream();
+  const cx<T>* tw = sp.twiddles(g.M);
+  const cx<T>* twrc = sp.rc_twiddles();
+  const long N = g.N;
+  AdvEpi<T> none{};
+  double bytes = (double)N * sizeof(T) * (1 + 1 + (e.stage == 1 ? 2 : 1));
+  if (g.d == 3) {
+    RowsIn<T, 3> in{{a, a + N, a + 2 * N}};
+    RowsOut<T, 3> out{{Q0, Q1, Q2}};
+    r2c<T, 3, true>(g, s, in, lam, out, 1 << 2, tw, twrc);
+    deriv<T>(g, sp, 1, Q1, Q2, Q2, s);
+    deriv<T>(g, sp, 0, Q0, Q2, Q2, s);
+    RowsSpec<T, 1> sp1{{Q2}};
+    c2r<T, 1, EPI_DIV>(g, s, sp1, 0, none, e, bytes, tw, twrc);
+  } else {
+    RowsIn<T, 2> in{{a, a + N}};
+    RowsOut<T, 2> out{{Q0, Q1}};
+    r2c<T, 2, true>(g, s, in, lam, out, 1 << 1, tw, twrc);
+    deriv<T>(g, sp, 0, Q0, Q1, Q1, s);
+    RowsSpec<T, 1> sp1{{Q1}};
+    c2r<T, 1, EPI_DIV>(g, s, sp1, 0, none, e, bytes, tw, twrc);
+  }
+}
+
+}  // namespace fused
+}  // namespace reg

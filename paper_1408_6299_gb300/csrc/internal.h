@@ -144,6 +144,23 @@ class Spectral {
 };
 
 // ---------------------------------------------------------------------------
+// Fused Heun stages (fused.cuh): advection k = -v.grad u [- grad m . v~] and
+// divergence k = div(v lam), each with its Runge-Kutta update in the last pass.
+// ---------------------------------------------------------------------------
+namespace fused {
+template <typename T>
+struct AdvEpi;
+template <typename T>
+struct DivEpi;
+}  // namespace fused
+// three packed-spectrum scratch buffers per call (Zx unused in 2D)
+template <typename T>
+void adv_stage(Spectral<T>& sp, const T* u, const fused::AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy);
+// a: d velocity fields at stride N
+template <typename T>
+void div_stage(Spectral<T>& sp, const T* lam, const T* a, const fused::DivEpi<T>& e, cx<T>* Q0, cx<T>* Q1, cx<T>* Q2);
+
+// ---------------------------------------------------------------------------
 // Fourier-diagonal operators on whole coefficient vectors (FP64), with the
 // DC/Nyquist pairing of the packed last-axis slot 0.
 // ---------------------------------------------------------------------------

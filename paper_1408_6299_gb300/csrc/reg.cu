@@ -19,6 +19,7 @@
 
 #include "../../include/reg.h"
 #include "internal.h"
+#include "fused.cuh"
 #include "pointwise.h"
 
 using namespace reg;
@@ -95,7 +96,7 @@ bool invert_small(int n, const std::vector<double>& A, std::vector<double>& Ai) 
 template <typename T>
 struct Work {
   using C = cx<T>;
-  DBuf<C> U, W;            // spectra
+  DBuf<C> U, W, X;         // spectra
   DBuf<T> G, q, va, vb, wa, wb;  // d fields
   DBuf<T> m, yh, acc, k, lam;    // fields
   DBuf<T> vcoef, wcoef;          // coefficient vectors in precision T
@@ -219,6 +220,41 @@ const T* vel_node(reg_ctx* c, const T* coef, int j, T* buf) {
   return buf;
 }
 
+// fused advection stage on u: k = -a.grad u [- gm.w], Heun stage update
+template <typename T>
+void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* y, T* out1, T* out2, T* Gkeep,
+         int stage) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), Nc = c->g.Nc;
+  fused::AdvEpi<T> e{};
+  for (int i = 0; i < c->d; ++i) {
+    e.a[i] = a + i * N;
+    e.gm[i] = gm ? gm + i * N : nullptr;
+    e.w[i] = gm ? wv + i * N : nullptr;
+    e.G[i] = Gkeep ? Gkeep + i * N : nullptr;
+  }
+  e.y = y;
+  e.out1 = out1;
+  e.out2 = out2;
+  e.h = (T)c->h();
+  e.stage = stage;
+  adv_stage<T>(spectral<T>(c), u, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
+}
+
+// fused divergence stage on lam: k = div(a lam), Heun stage update
+template <typename T>
+void divh(reg_ctx* c, const T* lam, const T* a, const T* y, T* out1, T* out2, int stage) {
+  Work<T>& w = work<T>(c);
+  const long Nc = c->g.Nc;
+  fused::DivEpi<T> e{};
+  e.y = y;
+  e.out1 = out1;
+  e.out2 = out2;
+  e.h = (T)c->h();
+  e.stage = stage;
+  div_stage<T>(spectral<T>(c), lam, a, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
+}
+
 // div(v lam) into out
 template <typename T>
 void div_vlam(reg_ctx* c, const T* vt, const T* lam, T* out) {
@@ -249,12 +285,10 @@ void state_steps(reg_ctx* c, const T* vcoef, int j0, int j1, T* gm, T* gmh, int 
   for (int j = j0; j < j1; ++j) {
     if (ck && c->ckpt > 0 && j % c->ckpt == 0)
       REG_CUDA(cudaMemcpyAsync(ck + (long)(j / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
-    T* G1 = gm ? gm + (long)(j - base) * dN : G;
-    grad_into<T>(c, m, G1);
-    transport_stage1<T>(G1, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, h, yh, acc, c->d, N, c->s);
-    T* G2 = gmh ? gmh + (long)(j + 1 - base) * dN : G;
-    grad_into<T>(c, yh, G2);
-    transport_stage2<T>(G2, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, h, m, c->d, N, c->s);
+    adv<T>(c, m, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, yh, acc, gm ? gm + (long)(j - base) * dN : nullptr,
+           1);
+    adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, m, nullptr,
+           gmh ? gmh + (long)(j + 1 - base) * dN : nullptr, 2);
   }
   if (ck && c->ckpt > 0 && j1 % c->ckpt == 0)
     REG_CUDA(cudaMemcpyAsync(ck + (long)(j1 / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
@@ -326,12 +360,10 @@ void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
                      c->s);
       else
         force_acc<T>(f, lam, gmh_slot<T>(c, j + 1, base), c->basis_at_node(j + 1, 0.5 * hd), c->n_c, c->d, N, c->s);
-      div_vlam<T>(c, vel_node<T>(c, vcoef, j + 1, vb), lam, k);
-      heun1<T>(k, lam, h, yh, acc, N, c->s);
+      divh<T>(c, lam, vel_node<T>(c, vcoef, j + 1, vb), lam, yh, acc, 1);
       if (c->quad)
         force_acc<T>(f, yh, gm_slot<T>(c, j, base), c->basis_at_node(j, 0.5 * hd), c->n_c, c->d, N, c->s);
-      div_vlam<T>(c, vel_node<T>(c, vcoef, j, va), yh, k);
-      heun2<T>(k, acc, h, lam, N, c->s);
+      divh<T>(c, yh, vel_node<T>(c, vcoef, j, va), acc, lam, nullptr, 2);
     }
     if (j0 == 0 && !c->quad)
       force_acc<T>(f, lam, gm_slot<T>(c, 0, base), c->basis_at_node(0, c->trap_w(0)), c->n_c, c->d, N, c->s);
@@ -369,12 +401,10 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
       if (j == 0) {
         transport_stage1<T>(nullptr, vA, g1, wA, nullptr, h, yh, acc, c->d, N, c->s);
       } else {
-        grad_into<T>(c, y, G);
-        transport_stage1<T>(G, vA, g1, wA, y, h, yh, acc, c->d, N, c->s);
+        adv<T>(c, y, vA, g1, wA, y, yh, acc, nullptr, 1);
       }
-      grad_into<T>(c, yh, G);
-      transport_stage2<T>(G, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, h, y, c->d,
-                          N, c->s);
+      adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, y, nullptr, nullptr,
+             2);
     }
   }
   // lam~_1 = -m~_1
