@@ -46,19 +46,31 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c_n(RowsIn<T, NF> in, const
   constexpr int RS = padded_len(M);
   __shared__ C buf[NF * RB * RS];
   const long row0 = (long)blockIdx.x * RB;
-  for (int e = threadIdx.x; e < NF * RB * M; e += kThreads) {
-    int f = e / (RB * M), rem = e % (RB * M);
-    int r = rem / M, j = rem % M;
-    long row = row0 + r;
-    C z = mk<C>(0, 0);
-    if (row < nrows) {
-      z = reinterpret_cast<const C*>(in.p[f])[row * M + j];
-      if (PROD) {
-        C l = reinterpret_cast<const C*>(lam)[row * M + j];
-        z = mk<C>(z.x * l.x, z.y * l.y);
-      }
+  // all global loads of a thread are issued before the first shared store;
+  // a thread takes every field of its points, so lam is read once per point
+  constexpr int PER = (RB * M + kThreads - 1) / kThreads;
+  C v[PER][NF];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    long row = row0 + e / M;
+    bool ok = e < RB * M && row < nrows;
+    long q = row * M + e % M;
+    C l = mk<C>(1, 1);
+    if (PROD && ok) l = reinterpret_cast<const C*>(lam)[q];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      C z = ok ? reinterpret_cast<const C*>(in.p[f])[q] : mk<C>(0, 0);
+      v[i][f] = PROD ? mk<C>(z.x * l.x, z.y * l.y) : z;
     }
-    buf[(f * RB + r) * RS + pad16(j)] = z;
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    if (e < RB * M) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) buf[(f * RB + e / M) * RS + pad16(e % M)] = v[i][f];
+    }
   }
   __syncthreads();
   smem_fft<T, M, false, kThreads, NF * RB>(buf, RS, tw);
@@ -98,7 +110,7 @@ struct AdvEpi {
   const T* gm[3];  // source: grad m at the stage time (null: no source)
   const T* w[3];   // source: incremental velocity at the stage time
   const T* y;      // stage 1: y_j (null = 0); stage 2: acc
-  T* out1;         // stage 1: y_j + h k; stage 2: acc + h/2 k
+  T* out1;         // stage 1: y_j + h k; stage 2: acc + h/2 k (null: only keep grad u)
   T* out2;         // stage 1: y_j + h/2 k
   T* G[3];         // optional: keep grad u (null: not stored)
   T h;
@@ -106,6 +118,10 @@ struct AdvEpi {
 };
 
 // Epilogue parameters of the divergence stage (adjoint / incremental adjoint).
+// Stage 1 can also accumulate the body force f_l,i += cA_l y gmA_i (+ cB_l out1
+// gmB_i): the trapezoid term of node j+1, or the two stage terms of the
+// discrete adjoint. The accumulator is f_hi (+ f_lo) with layout [n_c][d][N];
+// with f_lo set, (f_hi, f_lo) is a compensated pair (exact two-sum per add).
 template <typename T>
 struct DivEpi {
   const T* y;  // stage 1: lam_{j+1}; stage 2: acc
@@ -113,6 +129,13 @@ struct DivEpi {
   T* out2;
   T h;
   int stage;
+  T* f_hi;          // null: no force accumulation
+  T* f_lo;          // null: plain accumulation into f_hi
+  const T* gmA;     // d fields at stride N
+  const T* gmB;     // d fields or null
+  T cA[16], cB[16]; // per-coefficient weights
+  int nc, d;
+  long N;
 };
 
 template <typename T, int NF>
@@ -134,16 +157,28 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
   constexpr int RS = padded_len(M);
   __shared__ C buf[NF * RB * RS];
   const long row0 = (long)blockIdx.x * RB;
-  for (int e = threadIdx.x; e < NF * RB * M; e += kThreads) {
-    int f = e / (RB * M), rem = e % (RB * M);
-    int r = rem / M, j = rem % M;
-    long row = row0 + r;
-    C z = mk<C>(0, 0);
-    if (row < nrows) {
-      z = in.p[f][row * M + j];
-      if ((zmask >> f) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
+  constexpr int PER = (NF * RB * M + kThreads - 1) / kThreads;
+  C v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    v[i] = mk<C>(0, 0);
+    if (e < NF * RB * M) {
+      int f = e / (RB * M), rem = e % (RB * M);
+      long row = row0 + rem / M;
+      if (row < nrows) v[i] = in.p[f][row * M + rem % M];
     }
-    buf[(f * RB + r) * RS + pad16(j)] = z;
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    if (e < NF * RB * M) {
+      int f = e / (RB * M), rem = e % (RB * M);
+      int j = rem % M;
+      C z = v[i];
+      if ((zmask >> f) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
+      buf[(f * RB + rem / M) * RS + pad16(j)] = z;
+    }
   }
   __syncthreads();
   constexpr int H = M / 2 + 1;
@@ -182,6 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
 #pragma unroll
         for (int f = 0; f < NF; ++f) reinterpret_cast<C*>(adv.G[f])[q] = g[f];
       }
+      if (!adv.out1) continue;
       T k0 = 0, k1 = 0;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -210,8 +246,54 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
       C k = g[0];
       C yv = reinterpret_cast<const C*>(dv.y)[q];
       if (dv.stage == 1) {
-        reinterpret_cast<C*>(dv.out1)[q] = mk<C>(yv.x + dv.h * k.x, yv.y + dv.h * k.y);
+        C o1 = mk<C>(yv.x + dv.h * k.x, yv.y + dv.h * k.y);
+        reinterpret_cast<C*>(dv.out1)[q] = o1;
         reinterpret_cast<C*>(dv.out2)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
+        if (dv.f_hi) {
+          // products of the point pair with every component, then per
+          // coefficient all loads before any store
+          C ta[3], tb[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            ta[i] = tb[i] = mk<C>(0, 0);
+            if (i < dv.d) {
+              C ga = reinterpret_cast<const C*>(dv.gmA + i * dv.N)[q];
+              ta[i] = mk<C>(yv.x * ga.x, yv.y * ga.y);
+              if (dv.gmB) {
+                C gb = reinterpret_cast<const C*>(dv.gmB + i * dv.N)[q];
+                tb[i] = mk<C>(o1.x * gb.x, o1.y * gb.y);
+              }
+            }
+          }
+          for (int l = 0; l < dv.nc; ++l) {
+            C hi[3], lo[3];
+            C* H = reinterpret_cast<C*>(dv.f_hi + (long)l * dv.d * dv.N);
+            C* Lo = dv.f_lo ? reinterpret_cast<C*>(dv.f_lo + (long)l * dv.d * dv.N) : nullptr;
+            const long hN = dv.N / 2;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              if (i < dv.d) {
+                hi[i] = H[i * hN + q];
+                lo[i] = Lo ? Lo[i * hN + q] : mk<C>(0, 0);
+              }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              if (i < dv.d) {
+                T t0 = dv.cA[l] * ta[i].x + dv.cB[l] * tb[i].x;
+                T t1 = dv.cA[l] * ta[i].y + dv.cB[l] * tb[i].y;
+                if (Lo) {
+                  C h = hi[i];
+                  T s0 = h.x + t0, b0 = s0 - h.x, s1 = h.y + t1, b1 = s1 - h.y;
+                  lo[i].x += (h.x - (s0 - b0)) + (t0 - b0);
+                  lo[i].y += (h.y - (s1 - b1)) + (t1 - b1);
+                  H[i * hN + q] = mk<C>(s0, s1);
+                  Lo[i * hN + q] = lo[i];
+                } else {
+                  H[i * hN + q] = mk<C>(hi[i].x + t0, hi[i].y + t1);
+                }
+              }
+          }
+        }
       } else {
         reinterpret_cast<C*>(dv.out1)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
       }
@@ -229,9 +311,17 @@ __global__ void __launch_bounds__(kThreads) k_cols_deriv(const cx<T>* in, cx<T>*
   using C = cx<T>;
   __shared__ C buf[L * TC];
   const long off = (long)blockIdx.y * L * s + (long)blockIdx.x * TC;
-  for (int e = threadIdx.x; e < L * TC; e += kThreads) {
-    int j = e / TC, c = e % TC;
-    buf[j * TC + c] = in[off + (long)j * s + c];
+  constexpr int PER = (L * TC + kThreads - 1) / kThreads;
+  C v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    if (e < L * TC) v[i] = in[off + (long)(e / TC) * s + (e % TC)];
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    if (e < L * TC) buf[e] = v[i];
   }
   __syncthreads();
   smem_fft<T, L, true, kThreads, TC>(buf, TC, tw);
@@ -251,6 +341,178 @@ __global__ void __launch_bounds__(kThreads) k_cols_deriv(const cx<T>* in, cx<T>*
     if (add) z = cadd(z, add[o]);
     out[o] = z;
   }
+}
+
+// Same operator for lengths with a two-stage radix plan L = R0*R1, kept in
+// registers between stages. Forward: stage A (radix R0) straight from global
+// memory, shared exchange, stage B (radix R1, twiddles W_L^{r j}). After stage
+// B a thread holds the frequencies j + r*R0 (r < R1) of one column, which are
+// exactly the inputs of the first stage of an inverse transform planned as
+// (R1, R0); the multiplier and the conjugation happen in registers, then the
+// inverse stage A' (radix R1), a shared exchange, and stage B' (radix R0,
+// twiddles W_L^{r k} read transposed from the same table) writes to global
+// memory. Thread t owns column t % TC.
+template <typename T, int L, int TC, int R0, int R1>
+__global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv2(const cx<T>* in, cx<T>* out,
+                                                                                    const cx<T>* add, long s,
+                                                                                    const cx<T>* __restrict__ tw) {
+  using C = cx<T>;
+  constexpr int Q0 = L / R0;  // tasks per column of the radix-R0 stages
+  constexpr int Q1 = R0;      // tasks per column of the radix-R1 stages (L / R1)
+  constexpr int NT = TC * (Q0 > Q1 ? Q0 : Q1);
+  __shared__ C buf[L * TC];
+  const long off = (long)blockIdx.y * L * s + (long)blockIdx.x * TC;
+  const int b = threadIdx.x % TC, j = threadIdx.x / TC;
+  C v[R0 > R1 ? R0 : R1];
+  // forward stage A: x[j + r*Q0], r < R0
+  if (j < Q0) {
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[r] = in[off + (long)(j + r * Q0) * s + b];
+    Dft<T, R0>::run(v);
+#pragma unroll
+    for (int r = 0; r < R0; ++r) buf[(j * R0 + r) * TC + b] = v[r];
+  }
+  __syncthreads();
+  const T sc = (T)1 / (T)L;
+  if (j < Q1) {
+    // forward stage B: positions j + r*R0, twiddle W_L^{r j}
+#pragma unroll
+    for (int r = 0; r < R1; ++r) v[r] = buf[(j + r * R0) * TC + b];
+#pragma unroll
+    for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], __ldg(&tw[r * R0 + j]));
+    Dft<T, R1>::run(v);
+    // v[r] is frequency j + r*R0: conj(i k~ z / L) = (-k z.y, -k z.x) with k = k~ / L
+#pragma unroll
+    for (int r = 0; r < R1; ++r) {
+      T k = (T)kmask_l(j + r * R0, L) * sc;
+      v[r] = mk<C>(-k * v[r].y, -k * v[r].x);
+    }
+    // inverse stage A' (radix R1) on the same values: inputs j + r*R0 = j + r*(L/R1)
+    Dft<T, R1>::run(v);
+  }
+  __syncthreads();  // every thread has finished reading buf in stage B
+  if (j < Q1) {
+#pragma unroll
+    for (int r = 0; r < R1; ++r) buf[(j * R1 + r) * TC + b] = v[r];
+  }
+  __syncthreads();
+  if (j < Q0) {
+    // inverse stage B' (radix R0, previous radices R1): positions j + r*R1,
+    // twiddle W_L^{r j} = table entry [j*R0 + r]
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[r] = buf[(j + r * Q0) * TC + b];
+#pragma unroll
+    for (int r = 1; r < R0; ++r) v[r] = cmul(v[r], __ldg(&tw[j * R0 + r]));
+    Dft<T, R0>::run(v);
+#pragma unroll
+    for (int r = 0; r < R0; ++r) {
+      C z = cconj(v[r]);
+      long o = off + (long)(j + r * Q0) * s + b;
+      if (add) z = cadd(z, add[o]);
+      out[o] = z;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent, double-buffered form of k_cols_deriv2: each block walks tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; while it transforms tile t in
+// one shared buffer, asynchronous copies (cp.async, 16 bytes each) bring
+// tile t + gridDim.x into the other, so the memory system keeps streaming
+// during the FFT stages. A tile is TC neighbouring columns x L rows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T, int L, int TC, int NT>
+__device__ __forceinline__ void tile_prefetch(cx<T>* dst, const cx<T>* in, long off, long s) {
+  constexpr int PER16 = 16 / sizeof(cx<T>);  // complex values per 16-byte copy
+  constexpr int CHUNKS = L * TC / PER16;
+  for (int e = threadIdx.x; e < CHUNKS; e += NT) {
+    int row = (e * PER16) / TC, col = (e * PER16) % TC;
+    cp_async16(dst + row * TC + col, in + off + (long)row * s + col);
+  }
+}
+
+template <typename T, int L, int TC, int R0, int R1>
+__global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv2p(const cx<T>* in, cx<T>* out,
+                                                                                     const cx<T>* add, long s,
+                                                                                     long ntx, long ntiles,
+                                                                                     const cx<T>* __restrict__ tw) {
+  using C = cx<T>;
+  constexpr int Q0 = L / R0;
+  constexpr int Q1 = R0;
+  constexpr int NT = TC * (Q0 > Q1 ? Q0 : Q1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* bufs = reinterpret_cast<C*>(smem_raw);  // two tiles of L*TC
+  const int b = threadIdx.x % TC, j = threadIdx.x / TC;
+  const T sc = (T)1 / (T)L;
+  C v[R0 > R1 ? R0 : R1];
+  long t = blockIdx.x;
+  if (t < ntiles) tile_prefetch<T, L, TC, NT>(bufs, in, (t / ntx) * L * s + (t % ntx) * TC, s);
+  cp_async_commit();
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    C* cur = bufs + (it & 1) * L * TC;
+    C* nxt = bufs + ((it + 1) & 1) * L * TC;
+    const long off = (t / ntx) * L * s + (t % ntx) * TC;
+    const long tn = t + gridDim.x;
+    if (tn < ntiles) tile_prefetch<T, L, TC, NT>(nxt, in, (tn / ntx) * L * s + (tn % ntx) * TC, s);
+    cp_async_commit();
+    cp_async_wait_prev();  // this tile's copies have landed (the newest group may still fly)
+    __syncthreads();
+    // forward stage A from the staged tile
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[r] = cur[(j + r * Q0) * TC + b];
+      Dft<T, R0>::run(v);
+    }
+    __syncthreads();
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) cur[(j * R0 + r) * TC + b] = v[r];
+    }
+    __syncthreads();
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[r] = cur[(j + r * R0) * TC + b];
+#pragma unroll
+      for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], __ldg(&tw[r * R0 + j]));
+      Dft<T, R1>::run(v);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        T k = (T)kmask_l(j + r * R0, L) * sc;
+        v[r] = mk<C>(-k * v[r].y, -k * v[r].x);
+      }
+      Dft<T, R1>::run(v);
+    }
+    __syncthreads();
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) cur[(j * R1 + r) * TC + b] = v[r];
+    }
+    __syncthreads();
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[r] = cur[(j + r * Q0) * TC + b];
+#pragma unroll
+      for (int r = 1; r < R0; ++r) v[r] = cmul(v[r], __ldg(&tw[j * R0 + r]));
+      Dft<T, R0>::run(v);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        C z = cconj(v[r]);
+        long o = off + (long)(j + r * Q0) * s + b;
+        if (add) z = cadd(z, add[o]);
+        out[o] = z;
+      }
+    }
+    __syncthreads();  // cur is refilled by the prefetch of the iteration after next
+  }
+  cp_async_wait_prev();
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 }  // namespace fused

@@ -77,10 +77,46 @@ void deriv_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long ou
   REG_LAUNCH();
 }
 
+template <typename T, int L, int TC>
+void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
+                   cudaStream_t st) {
+  constexpr int R0 = Plan<L>::R[0], R1 = Plan<L>::R[1];
+  constexpr int NT = TC * (R0 > L / R0 ? R0 : L / R0);
+  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0));
+  const long ntx = s / TC, ntiles = ntx * outer;
+  constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
+  if (TC * sizeof(cx<T>) % 16 == 0 && ntiles >= 2 * 152) {
+    // persistent double-buffered form: as many resident blocks as fit
+    static int resident = 0;
+    if (resident == 0) {
+      auto kern = k_cols_deriv2p<T, L, TC, R0, R1>;
+      REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0, dev = 0, sms = 0;
+      REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+      REG_CUDA(cudaGetDevice(&dev));
+      REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      resident = (per_sm < 1 ? 1 : per_sm) * sms;
+    }
+    long grid = ntiles < resident ? ntiles : resident;
+    k_cols_deriv2p<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(in, out, add, s, ntx, ntiles, tw);
+    REG_LAUNCH();
+    return;
+  }
+  dim3 grid((unsigned)(s / TC), (unsigned)outer);
+  k_cols_deriv2<T, L, TC, R0, R1><<<grid, NT, 0, st>>>(in, out, add, s, tw);
+  REG_LAUNCH();
+}
+
 template <typename T, int L>
 void deriv_tc(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw, cudaStream_t st) {
   constexpr int TCmax0 = sizeof(T) == 4 ? 16 : 8;
   constexpr int TCmax = (L * TCmax0 * sizeof(cx<T>) > 32768) ? TCmax0 / 2 : TCmax0;
+  if constexpr (Plan<L>::S == 2) {
+    // two-stage plans keep the column in registers between the stages
+    if (s >= TCmax) return deriv2_launch<T, L, TCmax>(in, out, add, s, outer, tw, st);
+    if (s >= 4) return deriv2_launch<T, L, 4>(in, out, add, s, outer, tw, st);
+    return deriv2_launch<T, L, 2>(in, out, add, s, outer, tw, st);
+  }
   if (s >= TCmax) return deriv_launch<T, L, TCmax>(in, out, add, s, outer, tw, st);
   if (s >= 4) return deriv_launch<T, L, 4>(in, out, add, s, outer, tw, st);
   return deriv_launch<T, L, 2>(in, out, add, s, outer, tw, st);
@@ -116,8 +152,9 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
   RowsOut<T, 1> out1{{U}};
   r2c<T, 1, false>(g, s, in1, nullptr, out1, 0, tw, twrc);
   const int d = g.d;
-  double bytes = (double)g.N * sizeof(T) *
-                 (2 * d + (e.gm[0] ? 2 * d : 0) + (e.G[0] ? d : 0) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1));
+  double bytes = e.out1 ? (double)g.N * sizeof(T) *
+                             (2 * d + (e.gm[0] ? 2 * d : 0) + (e.G[0] ? d : 0) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1))
+                       : (double)g.N * sizeof(T) * 2 * d;
   DivEpi<T> none{};
   if (d == 3) {
     deriv<T>(g, sp, 1, U, Zy, nullptr, s);
@@ -141,6 +178,8 @@ void div_stage_impl(Spectral<T>& sp, const T* lam, const T* a, const DivEpi<T>& 
   const long N = g.N;
   AdvEpi<T> none{};
   double bytes = (double)N * sizeof(T) * (1 + 1 + (e.stage == 1 ? 2 : 1));
+  if (e.f_hi)
+    bytes += (double)N * sizeof(T) * (g.d * (e.gmB ? 2 : 1) + 2.0 * e.nc * g.d * (e.f_lo ? 2 : 1));
   if (g.d == 3) {
     RowsIn<T, 3> in{{a, a + N, a + 2 * N}};
     RowsOut<T, 3> out{{Q0, Q1, Q2}};

@@ -83,17 +83,34 @@ __global__ void k_products(const T* __restrict__ vt, const T* __restrict__ lam, 
   for (int i = 0; i < d; ++i) q[i * N + x] = vt[i * N + x] * l;
 }
 
-// f[l][i][x] += c_l lam[x] gm[i][x]   (double accumulation)
+// (f_hi, f_lo)[l][i][x] += c_l lam[x] gm[i][x]; with f_lo null a plain sum
+// into f_hi, else a compensated pair (the rounding error of each add kept in f_lo)
 template <typename T>
-__global__ void k_force(double* __restrict__ f, const T* __restrict__ lam, const T* __restrict__ gm, Coefs c,
-                        int nc, int d, long N) {
+__global__ void k_force(T* __restrict__ fhi, T* __restrict__ flo, const T* __restrict__ lam,
+                        const T* __restrict__ gm, Coefs c, int nc, int d, long N) {
   long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
-  double l = (double)lam[x];
+  T l = lam[x];
   for (int i = 0; i < d; ++i) {
-    double p = l * (double)gm[i * N + x];
-    for (int a = 0; a < nc; ++a) f[((long)a * d + i) * N + x] += c.c[a] * p;
+    T p = l * gm[i * N + x];
+    for (int a = 0; a < nc; ++a) {
+      long q = ((long)a * d + i) * N + x;
+      T t = (T)c.c[a] * p;
+      if (!flo) {
+        fhi[q] += t;
+      } else {
+        T h = fhi[q], sm = h + t, bp = sm - h;
+        flo[q] += (h - (sm - bp)) + (t - bp);
+        fhi[q] = sm;
+      }
+    }
   }
+}
+
+__global__ void k_pair_to_double(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ out,
+                                 long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)hi[i] + (double)lo[i];
 }
 
 // det F right-hand side for component q = (a,c): -v.grad F_q + sum_m gv_{am} F_{mc}
@@ -271,9 +288,14 @@ void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s) {
   REG_LAUNCH();
 }
 template <typename T>
-void force_acc(double* f, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s) {
-  ProfScope ps(KK_FORCE, s, (double)N * (sizeof(T) * (d + 1) + 16.0 * nc * d));
-  k_force<T><<<nblk(N), 256, 0, s>>>(f, lam, gm, c, nc, d, N);
+void force_acc(T* fhi, T* flo, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s) {
+  ProfScope ps(KK_FORCE, s, (double)N * sizeof(T) * ((d + 1) + 2.0 * nc * d * (flo ? 2 : 1)));
+  k_force<T><<<nblk(N), 256, 0, s>>>(fhi, flo, lam, gm, c, nc, d, N);
+  REG_LAUNCH();
+}
+
+void pair_to_double(const float* hi, const float* lo, double* out, long n, cudaStream_t s) {
+  k_pair_to_double<<<nblk(n), 256, 0, s>>>(hi, lo, out, n);
   REG_LAUNCH();
 }
 
@@ -285,7 +307,7 @@ void force_acc(double* f, const T* lam, const T* gm, const Coefs& c, int nc, int
   template void heun1<T>(const T*, const T*, T, T*, T*, long, cudaStream_t);                                \
   template void heun2<T>(const T*, const T*, T, T*, long, cudaStream_t);                                    \
   template void products<T>(const T*, const T*, T*, int, long, cudaStream_t);                               \
-  template void force_acc<T>(double*, const T*, const T*, const Coefs&, int, int, long, cudaStream_t);
+  template void force_acc<T>(T*, T*, const T*, const T*, const Coefs&, int, int, long, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -33,9 +33,12 @@ void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s);
 // q_i = v_i lam
 template <typename T>
 void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s);
-// f[l][i] += c_l lam gm_i in double precision
+// f[l][i] += c_l lam gm_i: plain sum into fhi (flo null) or a compensated
+// (fhi, flo) pair of precision T
 template <typename T>
-void force_acc(double* f, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s);
+void force_acc(T* fhi, T* flo, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s);
+// out = (double)hi + (double)lo
+void pair_to_double(const float* hi, const float* lo, double* out, long n, cudaStream_t s);
 
 void detF_rhs(const double* G, const double* vt, const double* gv, const double* F, int q, double* k, int d, long N,
               cudaStream_t s);

@@ -101,6 +101,7 @@ struct Work {
   DBuf<T> m, yh, acc, k, lam;    // fields
   DBuf<T> vcoef, wcoef;          // coefficient vectors in precision T
   DBuf<T> gm, gmh, ck;           // state gradients (all nodes or one segment), stage gradients, checkpoints
+  DBuf<T> fhi, flo;              // single precision body force as a compensated pair
 };
 
 }  // namespace
@@ -228,7 +229,7 @@ void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* 
   const long N = c->N(), Nc = c->g.Nc;
   fused::AdvEpi<T> e{};
   for (int i = 0; i < c->d; ++i) {
-    e.a[i] = a + i * N;
+    e.a[i] = a ? a + i * N : nullptr;
     e.gm[i] = gm ? gm + i * N : nullptr;
     e.w[i] = gm ? wv + i * N : nullptr;
     e.G[i] = Gkeep ? Gkeep + i * N : nullptr;
@@ -241,12 +242,19 @@ void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* 
   adv_stage<T>(spectral<T>(c), u, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
 }
 
-// fused divergence stage on lam: k = div(a lam), Heun stage update
+// grad u into G (d fields) through the fused stage passes
 template <typename T>
-void divh(reg_ctx* c, const T* lam, const T* a, const T* y, T* out1, T* out2, int stage) {
+void grad_fused(reg_ctx* c, const T* u, T* G) {
+  adv<T>(c, u, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, G, 1);
+}
+
+// fused divergence stage on lam: k = div(a lam), Heun stage update; e carries
+// the optional body-force accumulation of stage 1
+template <typename T>
+void divh(reg_ctx* c, const T* lam, const T* a, const T* y, T* out1, T* out2, int stage,
+          fused::DivEpi<T> e = fused::DivEpi<T>{}) {
   Work<T>& w = work<T>(c);
   const long Nc = c->g.Nc;
-  fused::DivEpi<T> e{};
   e.y = y;
   e.out1 = out1;
   e.out2 = out2;
@@ -292,7 +300,7 @@ void state_steps(reg_ctx* c, const T* vcoef, int j0, int j1, T* gm, T* gmh, int 
   }
   if (ck && c->ckpt > 0 && j1 % c->ckpt == 0)
     REG_CUDA(cudaMemcpyAsync(ck + (long)(j1 / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
-  if (gm) grad_into<T>(c, m, gm + (long)(j1 - base) * dN);
+  if (gm) grad_fused<T>(c, m, gm + (long)(j1 - base) * dN);
 }
 
 // Recompute state gradients of segment [j0, j1] from the checkpoint at j0.
@@ -331,21 +339,31 @@ void state_solve_store(reg_ctx* c, const T* vcoef, const T* m0) {
 }
 
 // Adjoint solve (Eq. first-order-adjoint) backward from lam (in w.lam at n_t),
-// accumulating the body force f_l = int b_l lam grad m dt (double) into f.
-// Leaves lam_0 in w.lam.
+// accumulating the body force f_l = int b_l lam grad m dt into f (double).
+// The force terms of each step are added in the first stage of the step: the
+// trapezoid term of node j+1, or the two stage terms of the discrete adjoint.
+// Single precision sweeps accumulate into a compensated pair of floats that is
+// converted to double at the end. Leaves lam_0 in w.lam.
 template <typename T>
 void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
   Work<T>& w = work<T>(c);
   const long N = c->N(), dN = c->dN();
   const double hd = c->h();
-  const T h = (T)hd;
   T* lam = w.lam.p;
   T* yh = w.yh.get(N);
   T* acc = w.acc.get(N);
-  T* k = w.k.get(N);
   T* va = w.va.get(dN);
   T* vb = w.vb.get(dN);
-  REG_CUDA(cudaMemsetAsync(f, 0, c->ncdN() * sizeof(double), c->s));
+  T* fhi;
+  T* flo = nullptr;
+  if (sizeof(T) == sizeof(double)) {
+    fhi = reinterpret_cast<T*>(f);
+  } else {
+    fhi = w.fhi.get(c->ncdN());
+    flo = w.flo.get(c->ncdN());
+    REG_CUDA(cudaMemsetAsync(flo, 0, c->ncdN() * sizeof(T), c->s));
+  }
+  REG_CUDA(cudaMemsetAsync(fhi, 0, c->ncdN() * sizeof(T), c->s));
   const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
   for (int seg = (c->n_t - 1) / K; seg >= 0; --seg) {
     int j0 = seg * K, j1 = j0 + K;
@@ -355,19 +373,32 @@ void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
       base = j0;
     }
     for (int j = j1 - 1; j >= j0; --j) {
-      if (!c->quad)
-        force_acc<T>(f, lam, gm_slot<T>(c, j + 1, base), c->basis_at_node(j + 1, c->trap_w(j + 1)), c->n_c, c->d, N,
-                     c->s);
-      else
-        force_acc<T>(f, lam, gmh_slot<T>(c, j + 1, base), c->basis_at_node(j + 1, 0.5 * hd), c->n_c, c->d, N, c->s);
-      divh<T>(c, lam, vel_node<T>(c, vcoef, j + 1, vb), lam, yh, acc, 1);
-      if (c->quad)
-        force_acc<T>(f, yh, gm_slot<T>(c, j, base), c->basis_at_node(j, 0.5 * hd), c->n_c, c->d, N, c->s);
+      fused::DivEpi<T> e{};
+      e.f_hi = fhi;
+      e.f_lo = flo;
+      e.nc = c->n_c;
+      e.d = c->d;
+      e.N = N;
+      if (!c->quad) {
+        e.gmA = gm_slot<T>(c, j + 1, base);
+        Coefs a = c->basis_at_node(j + 1, c->trap_w(j + 1));
+        for (int l = 0; l < c->n_c; ++l) e.cA[l] = (T)a.c[l];
+      } else {
+        e.gmA = gmh_slot<T>(c, j + 1, base);
+        e.gmB = gm_slot<T>(c, j, base);
+        Coefs a = c->basis_at_node(j + 1, 0.5 * hd), b = c->basis_at_node(j, 0.5 * hd);
+        for (int l = 0; l < c->n_c; ++l) {
+          e.cA[l] = (T)a.c[l];
+          e.cB[l] = (T)b.c[l];
+        }
+      }
+      divh<T>(c, lam, vel_node<T>(c, vcoef, j + 1, vb), lam, yh, acc, 1, e);
       divh<T>(c, yh, vel_node<T>(c, vcoef, j, va), acc, lam, nullptr, 2);
     }
     if (j0 == 0 && !c->quad)
-      force_acc<T>(f, lam, gm_slot<T>(c, 0, base), c->basis_at_node(0, c->trap_w(0)), c->n_c, c->d, N, c->s);
+      force_acc<T>(fhi, flo, lam, gm_slot<T>(c, 0, base), c->basis_at_node(0, c->trap_w(0)), c->n_c, c->d, N, c->s);
   }
+  if (flo) pair_to_double(reinterpret_cast<const float*>(fhi), reinterpret_cast<const float*>(flo), f, c->ncdN(), c->s);
 }
 
 // Incremental state solve forward from 0 (Eq. gauss-newton, first line), then
