@@ -55,6 +55,11 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-solves", action="store_true")
+    p.add_argument("--workload", default="matvec", choices=["matvec", "batch"])
+    p.add_argument("--pairs", type=int, default=256)
+    p.add_argument("--batch-sample", type=int, default=32)
+    p.add_argument("--workers", type=int, default=8)
     return p.parse_args()
 
 
@@ -196,6 +201,130 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# solve time to rel-grad 1e-2 (Alg. 1) on the 128^2 and 64^3 workloads
+# ----------------------------------------------------------------------------
+def solve_times():
+    import numpy as np
+    import torch
+
+    from paper_1408_6299_gb300 import lib, synth
+
+    out = {}
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    for c, precs in ((synth.blobs_2d(128), ("mixed", "fp64")), (synth.stokes_3d(64), ("mixed",))):
+        mT = dev(c["mT"])
+        for pname in precs:
+            prec = lib.REG_MIXED if pname == "mixed" else lib.REG_FP64
+            R = lib.Registration(c["n"], c["n_t"], c["n_c"], c["beta"], c["reg"], c["stokes"], prec)
+            mR = torch.empty(c["n"], dtype=torch.float64, device="cuda")
+            R.transport(dev(c["v_true"]), mT, mR)  # reference image by the library's own state solve
+            R.set_images(mT, mR)
+            v = torch.zeros(R.coef_shape(), dtype=torch.float64, device="cuda")
+            R.solve(v.clone(), grad_rtol=1e-2)  # warm-up (allocations, tables)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = R.solve(v, grad_rtol=1e-2, detF_substeps=4 if c["stokes"] else 0)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            ent = {"seconds": sec, "outer": rep["outer"], "pcg_iters": rep["pcg_iters"], "n_pde": rep["n_pde"],
+                   "grad_rel": rep["g_inf"] / rep["g0_inf"], "J_rel": rep["J"] / rep["J0"],
+                   "status": rep["status"]}
+            if c["stokes"]:
+                ent["detF_min_max"] = rep["detF"][:2]
+            out[f"{c['name']}-{pname}"] = ent
+            R.close()
+    return out
+
+
+# ----------------------------------------------------------------------------
+# batched 2D pairs (uneven sizes 64^2/128^2/256^2 at 4:2:1, H1, n_c = 1)
+# ----------------------------------------------------------------------------
+def batch_pairs(count):
+    import numpy as np
+
+    from paper_1408_6299_gb300 import synth
+    pairs = synth.batch_2d(count=count)
+    for p in pairs:
+        nt = 16  # doubled until the CFL number of the workload's max speed 0.3 is <= 0.2
+        while 0.3 * p["n"][0] / (2 * np.pi * nt) > 0.2:
+            nt *= 2
+        p["n_t"] = nt
+    return pairs
+
+
+def solve_pairs(pairs, workers):
+    """reference images by the library's own transport, then one batched solve;
+    returns (seconds of the solve call, reports)"""
+    import numpy as np
+    import torch
+
+    from paper_1408_6299_gb300 import lib
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    probs, ctxs = [], {}
+    for p in pairs:
+        key = (p["n"], p["n_t"], p["beta"])
+        if key not in ctxs:
+            ctxs[key] = lib.Registration(p["n"], p["n_t"], 1, p["beta"], lib.REG_H1, False, lib.REG_FP64)
+        mT = dev(p["mT"])
+        mR = torch.empty(p["n"], dtype=torch.float64, device="cuda")
+        ctxs[key].transport(dev(p["v_true"]), mT, mR)
+        probs.append(dict(n=p["n"], n_t=p["n_t"], n_c=1, beta=p["beta"], reg=lib.REG_H1, stokes=False, mT=mT,
+                          mR=mR, v=torch.zeros((1, 2) + p["n"], dtype=torch.float64, device="cuda")))
+    for R in ctxs.values():
+        R.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = lib.solve_batched(probs, precision=lib.REG_MIXED, workers=workers, grad_rtol=1e-2)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, reps
+
+
+def batch_sample(count, workers):
+    pairs = batch_pairs(count)
+    solve_pairs(pairs[:min(4, count)], workers)  # warm-up: tuning, tables
+    tb, reps = solve_pairs(pairs, workers)
+    ts, _ = solve_pairs(pairs, 1)
+    ok = sum(1 for r in reps if r["status"] == 0 and r["g_inf"] <= 1e-2 * r["g0_inf"])
+    return {"pairs": count, "workers": workers, "batched_solves_per_s": count / tb,
+            "sequential_solves_per_s": count / ts, "speedup": ts / tb, "converged": ok,
+            "mean_outer": sum(r["outer"] for r in reps) / count,
+            "mean_matvecs": sum(r["matvecs"] for r in reps) / count}
+
+
+def run_batch(args):
+    """--workload batch: the full batch, problems sharded across ranks"""
+    import torch
+
+    from paper_1408_6299_gb300.shard import partition
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pairs = batch_pairs(args.pairs)
+    mine = [pairs[i] for i in partition([p["n"][0] ** 2 * p["n_t"] for p in pairs], world)[rank]]
+    solve_pairs(mine[:4], args.workers)
+    if dist is not None:
+        dist.barrier()
+    t, reps = solve_pairs(mine, args.workers)
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    if rank == 0:
+        print(json.dumps({"metric": "batched 2D registration solves/s (rel-grad 1e-2)", "value": args.pairs / t,
+                          "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
+                          "data": "synthetic", "dtype": "f32",
+                          "config": {"workload": f"{args.pairs} 2D pairs 64^2/128^2/256^2 at 4:2:1, H1, n_c=1",
+                                     "workers_per_gpu": args.workers}}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args):
@@ -334,6 +463,9 @@ def run_ours(args):
                 "bytes_per_launch": prof["bytes"] / max(prof["launches"], 1),
                 "share_of_matvec": prof_all[dominant]["ms"] / max(sum(v["ms"] for v in prof_all.values()), 1e-9)}
 
+    solves = solve_times() if not args.no_solves else None
+    batch = batch_sample(args.batch_sample, args.workers) if (args.batch_sample > 0 and rank == 0) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -354,7 +486,7 @@ def run_ours(args):
                        "precision": "mixed (f32 sweeps, f64 force/tail/vectors)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "clocks": ck, "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "fp64": fp64,
-            "as_configured": as_cfg, "cpu_baseline": cpu,
+            "as_configured": as_cfg, "solve_to_rel_grad_1e-2": solves, "batch_2d": batch, "cpu_baseline": cpu,
             "kernel_ms_per_matvec": {k: round(v["ms"], 3) for k, v in prof_all.items()},
         }
         print(json.dumps(line), flush=True)
@@ -367,6 +499,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

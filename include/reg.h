@@ -215,6 +215,34 @@ REG_API void reg_solve_opts_default(reg_solve_opts* opts);
  * initial guess in, solution out (n_c*d*N). report (may be NULL): host. */
 REG_API reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report);
 
+/* One independent registration problem of a batch (Sec. 1.1 for each pair).
+ * m_T, m_R: N doubles each; v: initial guess in, solution out (n_c*d*N);
+ * each may be host or device memory. n[2] is ignored when d == 2. */
+typedef struct {
+  int d;
+  int64_t n[3];
+  int n_t;
+  int n_c;
+  double beta;
+  int reg_type;
+  int stokes;
+  const double* m_T;
+  const double* m_R;
+  double* v;
+} reg_problem;
+
+/* Solve `count` independent problems (Alg. 1 each, options opts for all, or
+ * the defaults when NULL) concurrently on the current device: `workers` host
+ * threads, each with its own CUDA stream and contexts cached per problem
+ * configuration, take problems from a queue ordered largest first. Contexts
+ * with their own stream replay the Hessian matvec as a captured CUDA graph.
+ * reports (may be NULL): host array of count, report i for problem i. Returns
+ * REG_OK when every solve returned REG_OK or REG_EMAXIT, else the status of
+ * the first failing problem (all problems are attempted); the message is in
+ * reg_last_error(NULL). Each problem's arrays must stay valid until return. */
+REG_API reg_status reg_solve_batched(const reg_problem* problems, int count, int precision, const reg_solve_opts* opts,
+                                     reg_solve_report* reports, int workers);
+
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the kernels).
  * Kernel kinds: 0 row real-to-complex FFT pass, 1 row complex-to-real pass,

@@ -1,6 +1,12 @@
 // fused_launch.cuh -- host launchers of the fused transport stages
 // (fused.cuh), instantiated once per precision by fused_f32.cu / fused_f64.cu.
 #pragma once
+#include <stdlib.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "fused.cuh"
 
 namespace reg {
@@ -77,16 +83,17 @@ void deriv_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long ou
   REG_LAUNCH();
 }
 
-template <typename T, int L, int TC>
+// variant 0: persistent double-buffered, tile width TCmax; variants 1..3:
+// one block per tile with widths TCmax, TCmax/2, 4
+template <typename T, int L, int TC, bool PERSIST>
 void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
                    cudaStream_t st) {
   constexpr int R0 = Plan<L>::R[0], R1 = Plan<L>::R[1];
   constexpr int NT = TC * (R0 > L / R0 ? R0 : L / R0);
   ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0));
   const long ntx = s / TC, ntiles = ntx * outer;
-  constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
-  if (TC * sizeof(cx<T>) % 16 == 0 && ntiles >= 2 * 152) {
-    // persistent double-buffered form: as many resident blocks as fit
+  if constexpr (PERSIST) {
+    constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
     static int resident = 0;
     if (resident == 0) {
       auto kern = k_cols_deriv2p<T, L, TC, R0, R1>;
@@ -99,23 +106,116 @@ void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long o
     }
     long grid = ntiles < resident ? ntiles : resident;
     k_cols_deriv2p<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(in, out, add, s, ntx, ntiles, tw);
-    REG_LAUNCH();
-    return;
+  } else {
+    dim3 grid((unsigned)(s / TC), (unsigned)outer);
+    k_cols_deriv2<T, L, TC, R0, R1><<<grid, NT, 0, st>>>(in, out, add, s, tw);
   }
-  dim3 grid((unsigned)(s / TC), (unsigned)outer);
-  k_cols_deriv2<T, L, TC, R0, R1><<<grid, NT, 0, st>>>(in, out, add, s, tw);
   REG_LAUNCH();
 }
 
 template <typename T, int L>
-void deriv_tc(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw, cudaStream_t st) {
+constexpr int tc_max() {
   constexpr int TCmax0 = sizeof(T) == 4 ? 16 : 8;
-  constexpr int TCmax = (L * TCmax0 * sizeof(cx<T>) > 32768) ? TCmax0 / 2 : TCmax0;
+  return (L * TCmax0 * sizeof(cx<T>) > 32768) ? TCmax0 / 2 : TCmax0;
+}
+
+template <typename T, int L>
+bool deriv2_variant_ok(int v, long s, long outer) {
+  constexpr int TM = tc_max<T, L>();
+  const int tc[4] = {TM, TM, TM / 2 >= 2 ? TM / 2 : 2, 4};
+  if (s < tc[v] || s % tc[v]) return false;
+  if (v == 0) return (s / TM) * outer >= 2 * 152;  // persistent form only for large grids
+  return true;
+}
+
+template <typename T, int L>
+void deriv2_variant(int v, const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
+                    cudaStream_t st) {
+  constexpr int TM = tc_max<T, L>();
+  switch (v) {
+    case 0: return deriv2_launch<T, L, TM, true>(in, out, add, s, outer, tw, st);
+    case 1: return deriv2_launch<T, L, TM, false>(in, out, add, s, outer, tw, st);
+    case 2: return deriv2_launch<T, L, (TM / 2 >= 2 ? TM / 2 : 2), false>(in, out, add, s, outer, tw, st);
+    default: return deriv2_launch<T, L, 4, false>(in, out, add, s, outer, tw, st);
+  }
+}
+
+// Autotuner of the column derivative pass: on the first use of a (precision,
+// length, stride, batch) shape every admissible variant runs three times on
+// scratch memory, timed with CUDA events on the calling stream, and the
+// fastest is kept for the process. REG_AUTOTUNE=0 skips the trials (the first
+// admissible variant in the order 0..3 is used).
+struct Tuner {
+  std::mutex mu;
+  std::map<std::tuple<int, int, long, long>, int> best;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+inline Tuner& tuner() {
+  static Tuner t;
+  return t;
+}
+
+template <typename T, int L>
+int deriv2_choice(long s, long outer, const cx<T>* tw, cudaStream_t st) {
+  Tuner& tu = tuner();
+  std::lock_guard<std::mutex> lk(tu.mu);
+  auto key = std::make_tuple((int)sizeof(T), L, s, outer);
+  auto it = tu.best.find(key);
+  if (it != tu.best.end()) return it->second;
+  int pick = -1;
+  const char* env = getenv("REG_AUTOTUNE");
+  bool tune = !(env && env[0] == '0');
+  const size_t field = (size_t)s * outer * L * sizeof(cx<T>);
+  if (tune && 2 * field > tu.scratch_bytes) {
+    if (tu.scratch) cudaFree(tu.scratch);
+    tu.scratch = nullptr;
+    tu.scratch_bytes = 0;
+    if (cudaMalloc(&tu.scratch, 2 * field) != cudaSuccess) {
+      (void)cudaGetLastError();
+      tune = false;
+    } else {
+      tu.scratch_bytes = 2 * field;
+    }
+  }
+  if (tune) {
+    cx<T>* a = (cx<T>*)tu.scratch;
+    cx<T>* b = a + s * outer * L;
+    REG_CUDA(cudaMemsetAsync(a, 0, field, st));
+    cudaEvent_t e0, e1;
+    REG_CUDA(cudaEventCreate(&e0));
+    REG_CUDA(cudaEventCreate(&e1));
+    float bestms = 1e30f;
+    for (int v = 0; v < 4; ++v) {
+      if (!deriv2_variant_ok<T, L>(v, s, outer)) continue;
+      deriv2_variant<T, L>(v, a, b, nullptr, s, outer, tw, st);  // first run (lazy set-up)
+      REG_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) deriv2_variant<T, L>(v, a, b, nullptr, s, outer, tw, st);
+      REG_CUDA(cudaEventRecord(e1, st));
+      REG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      REG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < bestms) {
+        bestms = ms;
+        pick = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  for (int v = 0; v < 4 && pick < 0; ++v)
+    if (deriv2_variant_ok<T, L>(v, s, outer)) pick = v;
+  tu.best[key] = pick;
+  return pick;
+}
+
+template <typename T, int L>
+void deriv_tc(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw, cudaStream_t st) {
+  constexpr int TCmax = tc_max<T, L>();
   if constexpr (Plan<L>::S == 2) {
     // two-stage plans keep the column in registers between the stages
-    if (s >= TCmax) return deriv2_launch<T, L, TCmax>(in, out, add, s, outer, tw, st);
-    if (s >= 4) return deriv2_launch<T, L, 4>(in, out, add, s, outer, tw, st);
-    return deriv2_launch<T, L, 2>(in, out, add, s, outer, tw, st);
+    int v = deriv2_choice<T, L>(s, outer, tw, st);
+    if (v >= 0) return deriv2_variant<T, L>(v, in, out, add, s, outer, tw, st);
   }
   if (s >= TCmax) return deriv_launch<T, L, TCmax>(in, out, add, s, outer, tw, st);
   if (s >= 4) return deriv_launch<T, L, 4>(in, out, add, s, outer, tw, st);

@@ -48,6 +48,7 @@ enum KernelKind {
   KK_COUNT = 7
 };
 void count_launch();
+void add_launches(long n);  // kernels launched by a graph replay
 long launch_count();
 
 struct KernelProfiler {

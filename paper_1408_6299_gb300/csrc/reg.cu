@@ -138,6 +138,16 @@ struct reg_ctx {
   // solve vectors
   DBuf<double> sv_g, sv_s, sv_r, sv_z, sv_p, sv_Hp, sv_vt;
   KernelProfiler prof;  // CUDA-event bracketing of launches by kind (off unless enabled)
+  // CUDA graph of the Hessian matvec (contexts with their own stream): the
+  // sweeps and the tail read the direction from gdir and write gout
+  bool graphs = false;
+  cudaGraphExec_t gexec = nullptr;
+  size_t gsig = 0;
+  long gkernels = 0;
+  DBuf<double> gdir, gout;
+  ~reg_ctx() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+  }
 
   long N() const { return g.N; }
   long ncdN() const { return (long)n_c * d * g.N; }
@@ -541,8 +551,7 @@ void gradient(reg_ctx* c, const double* v, double* g, double parts[2]) {
   c->ready = true;
 }
 
-void hessvec(reg_ctx* c, const double* vt, double* out) {
-  if (!c->ready) throw StatusError{REG_ENOTREADY, "no linearisation point: call reg_gradient or reg_linearize first"};
+void hessvec_body(reg_ctx* c, const double* vt, double* out) {
   double* f = c->f.get(c->ncdN());
   if (c->prec == REG_FP64) {
     gn_sweeps<double>(c, c->vlin.p, vt, f);
@@ -552,6 +561,62 @@ void hessvec(reg_ctx* c, const double* vt, double* out) {
     gn_sweeps<float>(c, c->w32.vcoef.p, w32, f);
   }
   tail(c, vt, f, out);
+}
+
+// addresses of every buffer the captured matvec touches: a change means the
+// graph would read or write stale memory and must be captured again
+size_t graph_signature(reg_ctx* c) {
+  const void* ptrs[] = {c->f.p,        c->SV.p,       c->SF.p,       c->vlin.p,     c->gdir.p,     c->gout.p,
+                        c->w64.U.p,    c->w64.W.p,    c->w64.X.p,    c->w64.m.p,    c->w64.yh.p,   c->w64.acc.p,
+                        c->w64.lam.p,  c->w64.va.p,   c->w64.vb.p,   c->w64.wa.p,   c->w64.wb.p,   c->w64.gm.p,
+                        c->w64.gmh.p,  c->w64.ck.p,   c->w32.U.p,    c->w32.W.p,    c->w32.X.p,    c->w32.m.p,
+                        c->w32.yh.p,   c->w32.acc.p,  c->w32.lam.p,  c->w32.va.p,   c->w32.vb.p,   c->w32.wa.p,
+                        c->w32.wb.p,   c->w32.gm.p,   c->w32.gmh.p,  c->w32.ck.p,   c->w32.vcoef.p, c->w32.wcoef.p,
+                        c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p};
+  size_t h = 1469598103934665603ull;
+  for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
+  return h;
+}
+
+void hessvec(reg_ctx* c, const double* vt, double* out) {
+  if (!c->ready) throw StatusError{REG_ENOTREADY, "no linearisation point: call reg_gradient or reg_linearize first"};
+  if (!c->graphs || !c->s || c->prof.mask) {
+    hessvec_body(c, vt, out);
+    return;
+  }
+  const long n = c->ncdN();
+  double* gvt = c->gdir.get(n);
+  double* gout = c->gout.get(n);
+  if (!c->gexec || graph_signature(c) != c->gsig) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    // one ordinary run allocates every buffer (and tunes the passes) first
+    REG_CUDA(cudaMemcpyAsync(gvt, vt, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    hessvec_body(c, gvt, gout);
+    REG_CUDA(cudaStreamSynchronize(c->s));
+    long l0 = launch_count();
+    cudaGraph_t graph = nullptr;
+    REG_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    try {
+      hessvec_body(c, gvt, gout);
+    } catch (...) {
+      cudaStreamEndCapture(c->s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    REG_CUDA(cudaStreamEndCapture(c->s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    REG_CUDA(e);
+    c->gkernels = launch_count() - l0;
+    c->gsig = graph_signature(c);
+  }
+  REG_CUDA(cudaMemcpyAsync(gvt, vt, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  REG_CUDA(cudaGraphLaunch(c->gexec, c->s));
+  add_launches(c->gkernels);
+  REG_CUDA(cudaMemcpyAsync(out, gout, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
 }
 
 Coefs basis_at(const reg_ctx* c, double t) {
@@ -808,6 +873,7 @@ reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, int n_c, 
     c->prec = precision;
     c->ckpt = ckpt_every;
     c->s = (cudaStream_t)cuda_stream;
+    c->graphs = c->s != nullptr;  // a context with its own stream replays its matvec as a CUDA graph
     for (int i = 0; i < d; ++i) c->hd *= 2.0 * M_PI / g.n[i];
     c->bnode.resize((size_t)(n_t + 1) * n_c);
     for (int j = 0; j <= n_t; ++j) cheb_values(n_c, (double)j / n_t, &c->bnode[(size_t)j * n_c]);

@@ -65,6 +65,21 @@ class SolveReport(ctypes.Structure):
         return out
 
 
+class ProblemC(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("n_t", ctypes.c_int),
+        ("n_c", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("reg_type", ctypes.c_int),
+        ("stokes", ctypes.c_int),
+        ("m_T", ctypes.c_void_p),
+        ("m_R", ctypes.c_void_p),
+        ("v", ctypes.c_void_p),
+    ]
+
+
 class RegError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -94,6 +109,8 @@ _SIGNATURES = {
     "reg_solve": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
     "reg_precond_noalloc": [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             _vp, _vp, _vp],
+    "reg_solve_batched": [ctypes.POINTER(ProblemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                          ctypes.POINTER(SolveReport), ctypes.c_int],
     "reg_profile_begin": [_vp, ctypes.c_uint],
     "reg_profile_end": [_vp, _vp, _vp, _vp],
 }
@@ -118,6 +135,35 @@ def precond_noalloc(n, n_c, beta, reg, r, z, stream=None):
     st = L.reg_precond_noalloc(len(n), arr, int(n_c), float(beta), int(reg), a, b, stream)
     if st != REG_OK:
         raise RegError(st, L.reg_last_error(None).decode())
+
+
+def solve_batched(problems, precision=REG_MIXED, workers=8, **opts):
+    """Solve independent problems concurrently (reg_solve_batched).
+
+    problems: list of dicts with keys n, n_t, n_c, beta, reg, stokes, mT, mR, v
+    (arrays as accepted by Registration; v is updated in place). Returns the
+    list of report dicts in the order of `problems`."""
+    L = load()
+    arr = (ProblemC * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        n = tuple(int(k) for k in p["n"])
+        a, ka = _addr(p["mT"])
+        b, kb = _addr(p["mR"])
+        c, kc = _addr(p["v"])
+        keep += [ka, kb, kc]
+        arr[i] = ProblemC(len(n), (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))), int(p["n_t"]),
+                          int(p.get("n_c", 1)), float(p["beta"]), int(p.get("reg", REG_H1)),
+                          int(bool(p.get("stokes", False))), a, b, c)
+    o = SolveOpts()
+    L.reg_solve_opts_default(ctypes.byref(o))
+    for k, val in opts.items():
+        setattr(o, k, val)
+    reps = (SolveReport * len(problems))()
+    st = L.reg_solve_batched(arr, len(problems), int(precision), ctypes.byref(o), reps, int(workers))
+    if st not in (REG_OK, REG_EMAXIT):
+        raise RegError(st, L.reg_last_error(None).decode())
+    return [r.as_dict() for r in reps]
 
 
 def library_path():
