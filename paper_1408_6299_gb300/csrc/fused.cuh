@@ -113,6 +113,9 @@ struct AdvEpi {
   T* out1;         // stage 1: y_j + h k; stage 2: acc + h/2 k (null: only keep grad u)
   T* out2;         // stage 1: y_j + h/2 k
   T* G[3];         // optional: keep grad u (null: not stored)
+  const T* src;    // optional precomputed source sum_i gm_i w_i (used instead of gm/w)
+  const T* sw[3];  // optional: with Sout, store Sout = sum_i (grad u)_i sw_i
+  T* Sout;
   T h;
   int stage;
 };
@@ -217,6 +220,16 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
 #pragma unroll
         for (int f = 0; f < NF; ++f) reinterpret_cast<C*>(adv.G[f])[q] = g[f];
       }
+      if (adv.Sout) {
+        T s0 = 0, s1 = 0;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          C w = reinterpret_cast<const C*>(adv.sw[f])[q];
+          s0 += g[f].x * w.x;
+          s1 += g[f].y * w.y;
+        }
+        reinterpret_cast<C*>(adv.Sout)[q] = mk<C>(s0, s1);
+      }
       if (!adv.out1) continue;
       T k0 = 0, k1 = 0;
 #pragma unroll
@@ -225,7 +238,11 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
         k0 -= a.x * g[f].x;
         k1 -= a.y * g[f].y;
       }
-      if (adv.gm[0]) {
+      if (adv.src) {
+        C sv = reinterpret_cast<const C*>(adv.src)[q];
+        k0 -= sv.x;
+        k1 -= sv.y;
+      } else if (adv.gm[0]) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           C gm = reinterpret_cast<const C*>(adv.gm[f])[q];

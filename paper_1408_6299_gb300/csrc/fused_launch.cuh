@@ -140,11 +140,16 @@ void deriv2_variant(int v, const cx<T>* in, cx<T>* out, const cx<T>* add, long s
   }
 }
 
-// Autotuner of the column derivative pass: on the first use of a (precision,
-// length, stride, batch) shape every admissible variant runs three times on
-// scratch memory, timed with CUDA events on the calling stream, and the
-// fastest is kept for the process. REG_AUTOTUNE=0 skips the trials (the first
-// admissible variant in the order 0..3 is used).
+// Autotuner of the column derivative pass. Fields larger than 16 MB stream
+// through DRAM (the input was written by the previous pass, partly still in
+// L2): there the persistent double-buffered variant is used whenever it is
+// admissible; isolated trials, warm or flushed, do not reproduce that state
+// and ranked the variants wrongly. Smaller fields live in L2 in use; on the
+// first use of such a (precision, length, stride, batch) shape every
+// admissible variant runs three times on scratch memory, timed with CUDA
+// events on the calling stream, and the fastest is kept for the process.
+// REG_AUTOTUNE=0 skips the trials (the first admissible variant in the order
+// 0..3 is used).
 struct Tuner {
   std::mutex mu;
   std::map<std::tuple<int, int, long, long>, int> best;
@@ -167,6 +172,10 @@ int deriv2_choice(long s, long outer, const cx<T>* tw, cudaStream_t st) {
   const char* env = getenv("REG_AUTOTUNE");
   bool tune = !(env && env[0] == '0');
   const size_t field = (size_t)s * outer * L * sizeof(cx<T>);
+  if (field > (16ull << 20) && deriv2_variant_ok<T, L>(0, s, outer)) {
+    tu.best[key] = 0;
+    return 0;
+  }
   if (tune && 2 * field > tu.scratch_bytes) {
     if (tu.scratch) cudaFree(tu.scratch);
     tu.scratch = nullptr;
@@ -189,14 +198,18 @@ int deriv2_choice(long s, long outer, const cx<T>* tw, cudaStream_t st) {
     for (int v = 0; v < 4; ++v) {
       if (!deriv2_variant_ok<T, L>(v, s, outer)) continue;
       deriv2_variant<T, L>(v, a, b, nullptr, s, outer, tw, st);  // first run (lazy set-up)
-      REG_CUDA(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; ++r) deriv2_variant<T, L>(v, a, b, nullptr, s, outer, tw, st);
-      REG_CUDA(cudaEventRecord(e1, st));
-      REG_CUDA(cudaEventSynchronize(e1));
-      float ms = 0;
-      REG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < bestms) {
-        bestms = ms;
+      float total = 0;
+      for (int r = 0; r < 3; ++r) {
+        REG_CUDA(cudaEventRecord(e0, st));
+        deriv2_variant<T, L>(v, a, b, nullptr, s, outer, tw, st);
+        REG_CUDA(cudaEventRecord(e1, st));
+        REG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        REG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        total += ms;
+      }
+      if (total < bestms) {
+        bestms = total;
         pick = v;
       }
     }
@@ -252,9 +265,9 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
   RowsOut<T, 1> out1{{U}};
   r2c<T, 1, false>(g, s, in1, nullptr, out1, 0, tw, twrc);
   const int d = g.d;
-  double bytes = e.out1 ? (double)g.N * sizeof(T) *
-                             (2 * d + (e.gm[0] ? 2 * d : 0) + (e.G[0] ? d : 0) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1))
-                       : (double)g.N * sizeof(T) * 2 * d;
+  double bytes = (double)g.N * sizeof(T) *
+                 (d + (e.G[0] ? d : 0) + (e.Sout ? d + 1 : 0) +
+                  (e.out1 ? d + (e.src ? 1 : (e.gm[0] ? 2 * d : 0)) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1) : 0));
   DivEpi<T> none{};
   if (d == 3) {
     deriv<T>(g, sp, 1, U, Zy, nullptr, s);

@@ -76,6 +76,15 @@ __global__ void k_heun2(const T* __restrict__ k, const T* __restrict__ acc, T h,
 }
 
 template <typename T>
+__global__ void k_dot_fields(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  T s = 0;
+  for (int i = 0; i < d; ++i) s += a[i * N + x] * b[i * N + x];
+  out[x] = s;
+}
+
+template <typename T>
 __global__ void k_products(const T* __restrict__ vt, const T* __restrict__ lam, T* __restrict__ q, int d, long N) {
   long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
@@ -282,6 +291,13 @@ void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s) {
   REG_LAUNCH();
 }
 template <typename T>
+void dot_fields(const T* a, const T* b, T* out, int d, long N, cudaStream_t s) {
+  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + 1));
+  k_dot_fields<T><<<nblk(N), 256, 0, s>>>(a, b, out, d, N);
+  REG_LAUNCH();
+}
+
+template <typename T>
 void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s) {
   ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + 1));
   k_products<T><<<nblk(N), 256, 0, s>>>(vt, lam, q, d, N);
@@ -307,6 +323,7 @@ void pair_to_double(const float* hi, const float* lo, double* out, long n, cudaS
   template void heun1<T>(const T*, const T*, T, T*, T*, long, cudaStream_t);                                \
   template void heun2<T>(const T*, const T*, T, T*, long, cudaStream_t);                                    \
   template void products<T>(const T*, const T*, T*, int, long, cudaStream_t);                               \
+  template void dot_fields<T>(const T*, const T*, T*, int, long, cudaStream_t);                             \
   template void force_acc<T>(T*, T*, const T*, const T*, const Coefs&, int, int, long, cudaStream_t);
 INST(float)
 INST(double)

@@ -30,6 +30,9 @@ template <typename T>
 void heun1(const T* k, const T* y, T h, T* yh, T* acc, long N, cudaStream_t s);
 template <typename T>
 void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s);
+// out = sum_i a_i b_i (d fields at stride N)
+template <typename T>
+void dot_fields(const T* a, const T* b, T* out, int d, long N, cudaStream_t s);
 // q_i = v_i lam
 template <typename T>
 void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s);

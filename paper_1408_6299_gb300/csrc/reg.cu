@@ -102,6 +102,7 @@ struct Work {
   DBuf<T> vcoef, wcoef;          // coefficient vectors in precision T
   DBuf<T> gm, gmh, ck;           // state gradients (all nodes or one segment), stage gradients, checkpoints
   DBuf<T> fhi, flo;              // single precision body force as a compensated pair
+  DBuf<T> src;                   // source grad m_j . v~(t_j) per node (all nodes or one segment)
 };
 
 }  // namespace
@@ -234,7 +235,7 @@ const T* vel_node(reg_ctx* c, const T* coef, int j, T* buf) {
 // fused advection stage on u: k = -a.grad u [- gm.w], Heun stage update
 template <typename T>
 void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* y, T* out1, T* out2, T* Gkeep,
-         int stage) {
+         int stage, const T* src = nullptr, const T* sw = nullptr, T* Sout = nullptr) {
   Work<T>& w = work<T>(c);
   const long N = c->N(), Nc = c->g.Nc;
   fused::AdvEpi<T> e{};
@@ -243,7 +244,10 @@ void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* 
     e.gm[i] = gm ? gm + i * N : nullptr;
     e.w[i] = gm ? wv + i * N : nullptr;
     e.G[i] = Gkeep ? Gkeep + i * N : nullptr;
+    e.sw[i] = sw ? sw + i * N : nullptr;
   }
+  e.src = src;
+  e.Sout = Sout;
   e.y = y;
   e.out1 = out1;
   e.out2 = out2;
@@ -322,6 +326,30 @@ void recompute_segment(reg_ctx* c, const T* vcoef, int j0, int j1) {
   REG_CUDA(cudaMemcpyAsync(m, w.ck.p + (long)(j0 / c->ckpt) * N, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
   state_steps<T>(c, vcoef, j0, j1, w.gm.get((size_t)(c->ckpt + 1) * dN),
                  c->quad ? w.gmh.get((size_t)(c->ckpt + 1) * dN) : nullptr, j0, nullptr);
+}
+
+// State re-advance over [j0, j1] from the checkpoint at j0 that keeps, instead
+// of the state gradients, the source s_j = grad m_j . w(t_j) of the
+// incremental state equation (slot j - j0); w: incremental velocity coefficients.
+template <typename T>
+void recompute_segment_src(reg_ctx* c, const T* vcoef, const T* wcoef, int j0, int j1) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  T* m = w.m.get(N);
+  T* yh = w.yh.get(N);
+  T* acc = w.acc.get(N);
+  T* va = w.va.get(dN);
+  T* vb = w.vb.get(dN);
+  T* wa = w.wa.get(dN);
+  T* src = w.src.get((size_t)(c->ckpt + 1) * N);
+  REG_CUDA(cudaMemcpyAsync(m, w.ck.p + (long)(j0 / c->ckpt) * N, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  for (int j = j0; j < j1; ++j) {
+    adv<T>(c, m, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, yh, acc, nullptr, 1, nullptr,
+           vel_node<T>(c, wcoef, j, wa), src + (long)(j - j0) * N);
+    adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, m, nullptr, nullptr, 2);
+  }
+  adv<T>(c, m, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, nullptr,
+         vel_node<T>(c, wcoef, j1, wa), src + (long)(j1 - j0) * N);
 }
 
 // Gradient slots available for node j (after ensure_segment)
@@ -413,6 +441,9 @@ void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
 
 // Incremental state solve forward from 0 (Eq. gauss-newton, first line), then
 // the incremental adjoint backward from -m~_1 with the incremental body force.
+// With the trapezoid quadrature the source grad m_j . v~(t_j) of every node is
+// formed once (during the state re-advance, or from the stored gradients) and
+// read as one field by both Heun stages.
 template <typename T>
 void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
   Work<T>& w = work<T>(c);
@@ -421,31 +452,49 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
   T* y = w.lam.get(N);  // the incremental state ends up as -lam~_1 in place
   T* yh = w.yh.get(N);
   T* acc = w.acc.get(N);
-  T* G = w.G.get(dN);
   T* va = w.va.get(dN);
   T* vb = w.vb.get(dN);
   T* wa = w.wa.get(dN);
   T* wb = w.wb.get(dN);
+  const bool use_src = !c->quad;
   const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
+  if (use_src && c->ckpt == 0) {
+    T* src = w.src.get((size_t)(c->n_t + 1) * N);
+    for (int j = 0; j <= c->n_t; ++j)
+      dot_fields<T>(gm_slot<T>(c, j, 0), vel_node<T>(c, wcoef, j, wa), src + (long)j * N, c->d, N, c->s);
+  }
   for (int seg = 0; seg * K < c->n_t; ++seg) {
     int j0 = seg * K, j1 = j0 + K;
     int base = 0;
     if (c->ckpt > 0) {
-      recompute_segment<T>(c, vcoef, j0, j1);
+      if (use_src) recompute_segment_src<T>(c, vcoef, wcoef, j0, j1);
+      else recompute_segment<T>(c, vcoef, j0, j1);
       base = j0;
     }
     for (int j = j0; j < j1; ++j) {
-      const T* g1 = gm_slot<T>(c, j, base);
-      const T* g2 = c->quad ? gmh_slot<T>(c, j + 1, base) : gm_slot<T>(c, j + 1, base);
       const T* vA = vel_node<T>(c, vcoef, j, va);
-      const T* wA = vel_node<T>(c, wcoef, j, wa);
-      if (j == 0) {
-        transport_stage1<T>(nullptr, vA, g1, wA, nullptr, h, yh, acc, c->d, N, c->s);
+      if (use_src) {
+        const T* s1 = w.src.p + (long)(j - base) * N;
+        const T* s2 = w.src.p + (long)(j + 1 - base) * N;
+        if (j == 0) {  // zero state: k1 = -s_0
+          lincomb_t<T>(-h, s1, (T)0, nullptr, yh, N, c->s);
+          lincomb_t<T>((T)(-0.5) * h, s1, (T)0, nullptr, acc, N, c->s);
+        } else {
+          adv<T>(c, y, vA, nullptr, nullptr, y, yh, acc, nullptr, 1, s1);
+        }
+        adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, y, nullptr, nullptr, 2, s2);
       } else {
-        adv<T>(c, y, vA, g1, wA, y, yh, acc, nullptr, 1);
+        const T* g1 = gm_slot<T>(c, j, base);
+        const T* g2 = gmh_slot<T>(c, j + 1, base);
+        const T* wA = vel_node<T>(c, wcoef, j, wa);
+        if (j == 0) {
+          transport_stage1<T>(nullptr, vA, g1, wA, nullptr, h, yh, acc, c->d, N, c->s);
+        } else {
+          adv<T>(c, y, vA, g1, wA, y, yh, acc, nullptr, 1);
+        }
+        adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, y, nullptr,
+               nullptr, 2);
       }
-      adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, y, nullptr, nullptr,
-             2);
     }
   }
   // lam~_1 = -m~_1
@@ -572,7 +621,7 @@ size_t graph_signature(reg_ctx* c) {
                         c->w64.gmh.p,  c->w64.ck.p,   c->w32.U.p,    c->w32.W.p,    c->w32.X.p,    c->w32.m.p,
                         c->w32.yh.p,   c->w32.acc.p,  c->w32.lam.p,  c->w32.va.p,   c->w32.vb.p,   c->w32.wa.p,
                         c->w32.wb.p,   c->w32.gm.p,   c->w32.gmh.p,  c->w32.ck.p,   c->w32.vcoef.p, c->w32.wcoef.p,
-                        c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p};
+                        c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p,    c->w64.src.p,  c->w32.src.p};
   size_t h = 1469598103934665603ull;
   for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
   return h;
