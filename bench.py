@@ -21,8 +21,8 @@ replica of the workload (the solver does not shard) and value counts the
 matvecs of all ranks over the slowest rank's time.
 
 --impl reference times the CPU oracle (oracle/) on the same workload: each
-step is one oracle matvec on the 256^3 grid with n_t = 2, and the n_t = 64
-cost is extrapolated from the n_t = 1 and n_t = 2 runs.
+step is one oracle matvec on the 256^3 grid with n_t = 2, and the cost of the
+n_t chosen above is extrapolated from the n_t = 1 and n_t = 2 runs.
 """
 import argparse
 import hashlib

@@ -822,6 +822,119 @@ int orc_hessvec(const orc_prob *P, const double *v, const double *mT, const doub
   return st;
 }
 
+/* Full Newton Hessian matvec (Eq. sec-order-opt-cond with the pressure
+ * eliminated, Eq. eliminated-icontrol; trapezoid quadrature only):
+ *   incremental state   as in orc_hessvec,
+ *   incremental adjoint -d/dt lt - div(v lt) - div(vt lam) = 0, lt_1 = -mt_1,
+ *                       Heun backward with the source s(t_j) = div(vt(t_j) lam_j),
+ *   body force          f~_l = sum_j w_j b_l(t_j) [lt_j grad m_j + lam_j grad mt_j],
+ *   out_l = beta sum C A vt_l' + K^gamma f~_l,
+ * with lam the adjoint of orc_gradient (lam_1 = m_R - m_1). */
+int orc_hessvec_newton(const orc_prob *P, const double *v, const double *mT, const double *mR, const double *vt,
+                       double *out) {
+  if (!prob_ok(P) || P->dto) return ORC_EINVAL;
+  long N = grid_N(P);
+  int d = P->d, nc = P->n_c, nt = P->n_t;
+  long T = nt + 1;
+  double h = 1.0 / nt;
+  double *mt = malloc(sizeof(double) * T * N), *gm = malloc(sizeof(double) * T * d * N);
+  double *lam = malloc(sizeof(double) * T * N), *mtil = malloc(sizeof(double) * T * N);
+  double *ltil = malloc(sizeof(double) * T * N), *f = calloc((long)nc * d * N, sizeof(double));
+  double *va = malloc(sizeof(double) * d * N), *vb = malloc(sizeof(double) * d * N);
+  double *wa = malloc(sizeof(double) * d * N), *wb = malloc(sizeof(double) * d * N);
+  double *k1 = malloc(sizeof(double) * N), *k2 = malloc(sizeof(double) * N), *yh = malloc(sizeof(double) * N);
+  double *sa = malloc(sizeof(double) * N), *sb = malloc(sizeof(double) * N);
+  double *gt = malloc(sizeof(double) * d * N), *wtmp = malloc(sizeof(double) * d * N);
+  int st = (!mt || !gm || !lam || !mtil || !ltil || !f || !va || !vb || !wa || !wb || !k1 || !k2 || !yh || !sa || !sb ||
+            !gt || !wtmp) ? ORC_ENOMEM : 0;
+  /* state, its gradients, and the adjoint from lam_1 = m_R - m_1 */
+  if (!st) st = orc_state(P, v, mT, mt, NULL);
+  if (!st) st = trajectory_gradients(P, mt, gm, 0);
+  if (!st) {
+    double *tmp = malloc(sizeof(double) * N);
+    if (!tmp) st = ORC_ENOMEM;
+    else {
+      for (long x = 0; x < N; ++x) tmp[x] = mR[x] - mt[(long)nt * N + x];
+      st = orc_adjoint(P, v, tmp, lam, NULL);
+      free(tmp);
+    }
+  }
+  /* incremental state, forward (as in orc_hessvec), keeping every node */
+  if (!st) memset(mtil, 0, sizeof(double) * N);
+  for (int j = 0; j < nt && !st; ++j) {
+    const double *y = mtil + (long)j * N;
+    double *yn = mtil + (long)(j + 1) * N;
+    velocity_at(P, v, j * h, va);
+    velocity_at(P, v, (j + 1) * h, vb);
+    velocity_at(P, vt, j * h, wa);
+    velocity_at(P, vt, (j + 1) * h, wb);
+    const double *g0 = gm + (long)j * d * N, *g1 = gm + (long)(j + 1) * d * N;
+    st = apply_L(P, va, y, k1, gt);
+    if (st) break;
+    for (long x = 0; x < N; ++x) {
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) s += g0[i * N + x] * wa[i * N + x];
+      k1[x] -= s;
+      yh[x] = y[x] + h * k1[x];
+    }
+    st = apply_L(P, vb, yh, k2, gt);
+    if (st) break;
+    for (long x = 0; x < N; ++x) {
+      double s = 0.0;
+      for (int i = 0; i < d; ++i) s += g1[i * N + x] * wb[i * N + x];
+      k2[x] -= s;
+      yn[x] = y[x] + 0.5 * h * (k1[x] + k2[x]);
+    }
+  }
+  /* incremental adjoint, backward from -mt_1, with the source div(vt lam) */
+  if (!st) {
+    for (long x = 0; x < N; ++x) ltil[(long)nt * N + x] = -mtil[(long)nt * N + x];
+    velocity_at(P, vt, 1.0, wb);
+    st = apply_D(P, wb, lam + (long)nt * N, sb, wtmp);
+  }
+  for (int j = nt - 1; j >= 0 && !st; --j) {
+    const double *l1 = ltil + (long)(j + 1) * N;
+    double *l0 = ltil + (long)j * N;
+    velocity_at(P, v, (j + 1) * h, vb);
+    velocity_at(P, v, j * h, va);
+    velocity_at(P, vt, j * h, wa);
+    st = apply_D(P, wa, lam + (long)j * N, sa, wtmp); /* source at t_j */
+    if (st) break;
+    st = apply_D(P, vb, l1, k1, wtmp);
+    if (st) break;
+    for (long x = 0; x < N; ++x) {
+      k1[x] += sb[x];
+      yh[x] = l1[x] + h * k1[x];
+    }
+    st = apply_D(P, va, yh, k2, wtmp);
+    if (st) break;
+    for (long x = 0; x < N; ++x) {
+      k2[x] += sa[x];
+      l0[x] = l1[x] + 0.5 * h * (k1[x] + k2[x]);
+    }
+    double *t = sa;
+    sa = sb;
+    sb = t; /* the source at t_j is the next step's source at t_{j+1} */
+  }
+  /* body force f~_l = sum_j w_j b_l(t_j) [lt_j grad m_j + lam_j grad mt_j] */
+  double b[64];
+  for (int j = 0; j <= nt && !st; ++j) {
+    double w = (j == 0 || j == nt) ? 0.5 * h : h;
+    orc_cheb_eval(nc, j * h, b);
+    st = orc_grad(P, mtil + (long)j * N, gt);
+    if (st) break;
+    const double *lt = ltil + (long)j * N, *lj = lam + (long)j * N, *g = gm + (long)j * d * N;
+    for (long x = 0; x < N; ++x)
+      for (int l = 0; l < nc; ++l)
+        for (int i = 0; i < d; ++i)
+          f[((long)l * d + i) * N + x] += w * b[l] * (lt[x] * g[i * N + x] + lj[x] * gt[i * N + x]);
+  }
+  if (!st) st = control_tail(P, vt, f, out);
+  free(mt); free(gm); free(lam); free(mtil); free(ltil); free(f); free(va); free(vb); free(wa); free(wb);
+  free(k1); free(k2); free(yh); free(sa); free(sb); free(gt); free(wtmp);
+  return st;
+}
+
 /* ------------------------------------------------------------------ */
 /* Deformation gradient (App. D Eq. def-grad) and CFL number (Sec. 3.3.1) */
 /* ------------------------------------------------------------------ */

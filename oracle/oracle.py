@@ -100,6 +100,7 @@ def lib():
                 "orc_objective": [P, dp, dp, dp, dp],
                 "orc_gradient": [P, dp, dp, dp, dp, dp],
                 "orc_hessvec": [P, dp, dp, dp, dp],
+                "orc_hessvec_newton": [P, dp, dp, dp, dp, dp],
                 "orc_detF": [P, dp, dp],
                 "orc_solve": [P, ctypes.POINTER(Opts), dp, dp, dp, ctypes.POINTER(Report)],
             }.items():
@@ -228,6 +229,14 @@ class Problem:
         vt = _f64(vt).reshape(self.coef_shape())
         out = np.empty(self.coef_shape())
         self._call("orc_hessvec", _ptr(v), _ptr(_f64(mT)), _ptr(vt), _ptr(out))
+        return out
+
+    def hessvec_newton(self, v, mT, mR, vt):
+        """Full Newton Hessian matvec (trapezoid quadrature)."""
+        v = _f64(v).reshape(self.coef_shape())
+        vt = _f64(vt).reshape(self.coef_shape())
+        out = np.empty(self.coef_shape())
+        self._call("orc_hessvec_newton", _ptr(v), _ptr(_f64(mT)), _ptr(_f64(mR)), _ptr(vt), _ptr(out))
         return out
 
     def detF(self, v):

@@ -553,3 +553,40 @@ def test_solve_smooth_problem():
     assert 2 <= rep["outer"] <= 8
     assert rep["ls_trials"] == rep["outer"]  # alpha = 1 accepted every time
     assert rep["J"] < 0.5 * rep["J0"]
+
+
+# ---------------------------------------------------------------------------
+# Full Newton Hessian (Eq. sec-order-opt-cond, Sec. 3.2.1): equals Gauss-Newton
+# where lambda vanishes, and is the derivative of the (trapezoid) gradient up
+# to O(h_t^2), while Gauss-Newton keeps an O(1) gap there.
+# ---------------------------------------------------------------------------
+
+def newton_setup(nt):
+    c = synth.sinusoid_2d()
+    P = O.Problem(c["n"], nt, 1, c["beta"], 1, False)
+    mR = O.Problem(c["n"], 16).state(c["v_true"], c["mT"])[-1]
+    return c, P, mR
+
+
+def test_newton_equals_gauss_newton_at_the_inverse_crime_point():
+    c = synth.stokes_3d(16, n_t=6, n_c=2)
+    P = O.Problem(c["n"], 6, 2, c["beta"], 1, True)
+    mR = P.state(c["v_true"], c["mT"])[-1]  # lambda = 0 at v_true
+    Hn = P.hessvec_newton(c["v_true"], c["mT"], mR, c["vt"])
+    Hg = P.hessvec(c["v_true"], c["mT"], c["vt"])
+    assert np.abs(Hn - Hg).max() <= 1e-14 * np.abs(Hg).max()
+
+
+def test_newton_is_the_gradient_derivative_at_second_order():
+    errs_n, errs_g = [], []
+    for nt in (16, 32, 64):
+        c, P, mR = newton_setup(nt)
+        v = 0.5 * c["v_true"]
+        eps = 1e-5
+        fd = (P.gradient(v + eps * c["vt"], c["mT"], mR)[0] - P.gradient(v - eps * c["vt"], c["mT"], mR)[0]) / (2 * eps)
+        errs_n.append(np.linalg.norm(P.hessvec_newton(v, c["mT"], mR, c["vt"]) - fd) / np.linalg.norm(fd))
+        errs_g.append(np.linalg.norm(P.hessvec(v, c["mT"], c["vt"]) - fd) / np.linalg.norm(fd))
+    rates = np.log2(np.array(errs_n[:-1]) / np.array(errs_n[1:]))
+    assert np.all(np.abs(rates - 2) < 0.2), (errs_n, rates)
+    assert errs_n[-1] < 1e-5
+    assert min(errs_g) > 1e3 * errs_n[-1]  # the lambda terms are not negligible here
