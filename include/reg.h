@@ -97,6 +97,19 @@ REG_API const char* reg_last_error(const reg_ctx* ctx);
 /* Choose the time quadrature of the body force (default trapezoid). */
 REG_API reg_status reg_set_quadrature(reg_ctx* ctx, int quadrature);
 
+typedef enum {
+  REG_HESS_GN = 0,     /* Gauss-Newton: all lambda terms dropped (Sec. 3.2.2, Eq. gauss-newton) */
+  REG_HESS_NEWTON = 1  /* full Newton (Eq. sec-order-opt-cond): the incremental adjoint carries
+                          -div(v~ lam) and the body force lam grad m~ (trapezoid quadrature only) */
+} reg_hessian;
+
+/* Choose the Hessian applied by reg_hessvec and reg_solve (default
+ * Gauss-Newton). The full Newton matvec re-advances the adjoint alongside the
+ * incremental adjoint and keeps the incremental state of every time node
+ * ((n_t+1)*N values). Invalidates the linearisation point. REG_EINVAL with the
+ * discrete quadrature. */
+REG_API reg_status reg_set_hessian(reg_ctx* ctx, int kind);
+
 /* Copy the template m_T and the reference m_R (N values each) into the
  * context (Sec. 1.1). Invalidates the linearisation point. */
 REG_API reg_status reg_set_images(reg_ctx* ctx, const double* m_T, const double* m_R);

@@ -60,6 +60,7 @@ typedef struct {
   double backtrack;      /* step reduction factor */
   int max_backtracks;    /* line-search trials */
   int pcg_maxit;         /* 0: use n (order of the reduced system) */
+  int newton;            /* 1: full Newton Hessian in PCG (N-PCG), else Gauss-Newton */
 } orc_opts;
 
 typedef struct {
@@ -1036,7 +1037,8 @@ double orc_cfl(const orc_prob *P, const double *v) {
 
 /* ------------------------------------------------------------------ */
 /* Inexact Gauss-Newton-Krylov solve (Alg. 1; PCG per Eq.              */
-/* termination-criterion-ksm; Armijo backtracking, Sec. 3.2)           */
+/* termination-criterion-ksm; Armijo backtracking, Sec. 3.2); with     */
+/* opts.newton the full Newton matvec (N-PCG of Sec. 4)                */
 /* ------------------------------------------------------------------ */
 
 static double dot(long n, const double *a, const double *b) {
@@ -1087,7 +1089,7 @@ int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const doub
     double rz = dot(n, r, z);
     for (long it = 0; it < maxit && !st; ++it) {
       if (sqrt(dot(n, r, r)) <= eta * g2) break;
-      st = orc_hessvec(P, v, mT, p, Hp);
+      st = O->newton ? orc_hessvec_newton(P, v, mT, mR, p, Hp) : orc_hessvec(P, v, mT, p, Hp);
       R->matvecs += 1;
       R->n_pde += 2;
       R->pcg_iters += 1;

@@ -46,6 +46,7 @@ class Opts(ctypes.Structure):
         ("backtrack", ctypes.c_double),
         ("max_backtracks", ctypes.c_int),
         ("pcg_maxit", ctypes.c_int),
+        ("newton", ctypes.c_int),
     ]
 
 
@@ -250,9 +251,11 @@ class Problem:
         return float(lib().orc_cfl(ctypes.byref(self._p), _ptr(v)))
 
     def solve(self, mT, mR, v0=None, grad_rtol=1e-2, max_outer=50, armijo_c1=1e-4, backtrack=0.5,
-              max_backtracks=20, pcg_maxit=0):
+              max_backtracks=20, pcg_maxit=0, newton=False):
         v = np.zeros(self.coef_shape()) if v0 is None else _f64(v0).reshape(self.coef_shape()).copy()
-        opts = Opts(grad_rtol, max_outer, armijo_c1, backtrack, max_backtracks, pcg_maxit)
+        if newton and self.dto:
+            raise ValueError("the full Newton Hessian uses the trapezoid quadrature")
+        opts = Opts(grad_rtol, max_outer, armijo_c1, backtrack, max_backtracks, pcg_maxit, int(bool(newton)))
         rep = Report()
         st = lib().orc_solve(ctypes.byref(self._p), ctypes.byref(opts), _ptr(_f64(mT)), _ptr(_f64(mR)),
                              _ptr(v), ctypes.byref(rep))

@@ -125,6 +125,9 @@ struct AdvEpi {
 // gmB_i): the trapezoid term of node j+1, or the two stage terms of the
 // discrete adjoint. The accumulator is f_hi (+ f_lo) with layout [n_c][d][N];
 // with f_lo set, (f_hi, f_lo) is a compensated pair (exact two-sum per add).
+// Stage 0 only evaluates: out1 = div(v lam) (+ src). src (optional) is added
+// to the divergence (the div(v~ lam) source of the full Newton incremental
+// adjoint). gmC/yC (optional) add the Newton force term cA_l yC gmC_i.
 template <typename T>
 struct DivEpi {
   const T* y;  // stage 1: lam_{j+1}; stage 2: acc
@@ -139,6 +142,9 @@ struct DivEpi {
   T cA[16], cB[16]; // per-coefficient weights
   int nc, d;
   long N;
+  const T* src;     // added to the divergence
+  const T* gmC;     // d fields or null
+  const T* yC;
 };
 
 template <typename T, int NF>
@@ -261,6 +267,14 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
       }
     } else {
       C k = g[0];
+      if (dv.src) {
+        C sv = reinterpret_cast<const C*>(dv.src)[q];
+        k = mk<C>(k.x + sv.x, k.y + sv.y);
+      }
+      if (dv.stage == 0) {
+        reinterpret_cast<C*>(dv.out1)[q] = k;
+        continue;
+      }
       C yv = reinterpret_cast<const C*>(dv.y)[q];
       if (dv.stage == 1) {
         C o1 = mk<C>(yv.x + dv.h * k.x, yv.y + dv.h * k.y);
@@ -276,6 +290,11 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
             if (i < dv.d) {
               C ga = reinterpret_cast<const C*>(dv.gmA + i * dv.N)[q];
               ta[i] = mk<C>(yv.x * ga.x, yv.y * ga.y);
+              if (dv.gmC) {
+                C gc = reinterpret_cast<const C*>(dv.gmC + i * dv.N)[q];
+                C yc = reinterpret_cast<const C*>(dv.yC)[q];
+                ta[i] = mk<C>(ta[i].x + yc.x * gc.x, ta[i].y + yc.y * gc.y);
+              }
               if (dv.gmB) {
                 C gb = reinterpret_cast<const C*>(dv.gmB + i * dv.N)[q];
                 tb[i] = mk<C>(o1.x * gb.x, o1.y * gb.y);

@@ -290,9 +290,10 @@ void div_stage_impl(Spectral<T>& sp, const T* lam, const T* a, const DivEpi<T>& 
   const cx<T>* twrc = sp.rc_twiddles();
   const long N = g.N;
   AdvEpi<T> none{};
-  double bytes = (double)N * sizeof(T) * (1 + 1 + (e.stage == 1 ? 2 : 1));
+  double bytes = (double)N * sizeof(T) * (1 + (e.stage ? 1 : 0) + (e.stage == 1 ? 2 : 1) + (e.src ? 1 : 0));
   if (e.f_hi)
-    bytes += (double)N * sizeof(T) * (g.d * (e.gmB ? 2 : 1) + 2.0 * e.nc * g.d * (e.f_lo ? 2 : 1));
+    bytes += (double)N * sizeof(T) *
+             (g.d * (e.gmB ? 2 : 1) + (e.gmC ? g.d + 1 : 0) + 2.0 * e.nc * g.d * (e.f_lo ? 2 : 1));
   if (g.d == 3) {
     RowsIn<T, 3> in{{a, a + N, a + 2 * N}};
     RowsOut<T, 3> out{{Q0, Q1, Q2}};

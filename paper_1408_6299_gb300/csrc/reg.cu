@@ -103,12 +103,14 @@ struct Work {
   DBuf<T> gm, gmh, ck;           // state gradients (all nodes or one segment), stage gradients, checkpoints
   DBuf<T> fhi, flo;              // single precision body force as a compensated pair
   DBuf<T> src;                   // source grad m_j . v~(t_j) per node (all nodes or one segment)
+  DBuf<T> mtil, lamN, yh2, acc2, st0, st1, Gt, mR, m1;  // full Newton matvec
 };
 
 }  // namespace
 
 struct reg_ctx {
   int d = 0, n_t = 0, n_c = 0, rtype = 1, stokes = 0, prec = 0, ckpt = 0, quad = 0;
+  int hess = 0;  // REG_HESS_GN or REG_HESS_NEWTON
   double beta = 0;
   cudaStream_t s = nullptr;
   Grid g;
@@ -439,6 +441,85 @@ void adjoint_solve(reg_ctx* c, const T* vcoef, double* f) {
   if (flo) pair_to_double(reinterpret_cast<const float*>(fhi), reinterpret_cast<const float*>(flo), f, c->ncdN(), c->s);
 }
 
+// Full Newton incremental adjoint (Eq. sec-order-iadj / sec-order-icontrol,
+// trapezoid quadrature): backward from lam~_1 (in w.lam) with the source
+// div(v~ lam); the adjoint lam itself is re-advanced alongside from
+// lam_1 = m_R - m_1, so no adjoint trajectory is stored. The body force gains
+// lam_j grad m~_j, with m~_j kept by the forward sweep. Per step: the
+// incremental stage 1 (force of node j+1, source at t_{j+1}), the two adjoint
+// stages, the source at t_j, the incremental stage 2.
+template <typename T>
+void newton_adjoint(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
+  Work<T>& w = work<T>(c);
+  const long N = c->N(), dN = c->dN();
+  T* lt = w.lam.p;  // lam~
+  T* yh = w.yh.get(N);
+  T* acc = w.acc.get(N);
+  T* lam = w.lamN.get(N);
+  T* yh2 = w.yh2.get(N);
+  T* acc2 = w.acc2.get(N);
+  T* sA = w.st0.get(N);
+  T* sB = w.st1.get(N);
+  T* Gt = w.Gt.get(dN);
+  T* va = w.va.get(dN);
+  T* vb = w.vb.get(dN);
+  T* wa = w.wa.get(dN);
+  const T* mtil = w.mtil.p;
+  T* fhi;
+  T* flo = nullptr;
+  if (sizeof(T) == sizeof(double)) {
+    fhi = reinterpret_cast<T*>(f);
+  } else {
+    fhi = w.fhi.get(c->ncdN());
+    flo = w.flo.get(c->ncdN());
+    REG_CUDA(cudaMemsetAsync(flo, 0, c->ncdN() * sizeof(T), c->s));
+  }
+  REG_CUDA(cudaMemsetAsync(fhi, 0, c->ncdN() * sizeof(T), c->s));
+  // lam_1 = m_R - m_1 and the source at t_1
+  lincomb_t<T>((T)1, w.mR.p, (T)-1, w.m1.p, lam, N, c->s);
+  divh<T>(c, lam, vel_node<T>(c, wcoef, c->n_t, wa), nullptr, sB, nullptr, 0);
+  const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
+  for (int seg = (c->n_t - 1) / K; seg >= 0; --seg) {
+    int j0 = seg * K, j1 = j0 + K;
+    int base = 0;
+    if (c->ckpt > 0) {
+      recompute_segment<T>(c, vcoef, j0, j1);
+      base = j0;
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      // incremental stage 1 at t_{j+1}, with the force of node j+1
+      grad_fused<T>(c, mtil + (long)(j + 1) * N, Gt);
+      fused::DivEpi<T> e{};
+      e.f_hi = fhi;
+      e.f_lo = flo;
+      e.nc = c->n_c;
+      e.d = c->d;
+      e.N = N;
+      e.gmA = gm_slot<T>(c, j + 1, base);
+      e.gmC = Gt;
+      e.yC = lam;
+      Coefs a = c->basis_at_node(j + 1, c->trap_w(j + 1));
+      for (int l = 0; l < c->n_c; ++l) e.cA[l] = (T)a.c[l];
+      e.src = sB;
+      const T* vB = vel_node<T>(c, vcoef, j + 1, vb);
+      const T* vA = vel_node<T>(c, vcoef, j, va);
+      divh<T>(c, lt, vB, lt, yh, acc, 1, e);
+      // adjoint step lam_{j+1} -> lam_j
+      divh<T>(c, lam, vB, lam, yh2, acc2, 1);
+      divh<T>(c, yh2, vA, acc2, lam, nullptr, 2);
+      // source at t_j, then incremental stage 2
+      divh<T>(c, lam, vel_node<T>(c, wcoef, j, wa), nullptr, sA, nullptr, 0);
+      fused::DivEpi<T> e2{};
+      e2.src = sA;
+      divh<T>(c, yh, vA, acc, lt, nullptr, 2, e2);
+      std::swap(sA, sB);  // the source at t_j is the next step's source at t_{j+1}
+    }
+    if (j0 == 0)  // node 0: m~_0 = 0, so only the Gauss-Newton term
+      force_acc<T>(fhi, flo, lt, gm_slot<T>(c, 0, base), c->basis_at_node(0, c->trap_w(0)), c->n_c, c->d, N, c->s);
+  }
+  if (flo) pair_to_double(reinterpret_cast<const float*>(fhi), reinterpret_cast<const float*>(flo), f, c->ncdN(), c->s);
+}
+
 // Incremental state solve forward from 0 (Eq. gauss-newton, first line), then
 // the incremental adjoint backward from -m~_1 with the incremental body force.
 // With the trapezoid quadrature the source grad m_j . v~(t_j) of every node is
@@ -458,6 +539,11 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
   T* wb = w.wb.get(dN);
   const bool use_src = !c->quad;
   const int K = c->ckpt > 0 ? c->ckpt : c->n_t;
+  T* mtil = nullptr;
+  if (c->hess == REG_HESS_NEWTON) {  // keep every node of the incremental state
+    mtil = w.mtil.get((size_t)(c->n_t + 1) * N);
+    REG_CUDA(cudaMemsetAsync(mtil, 0, N * sizeof(T), c->s));
+  }
   if (use_src && c->ckpt == 0) {
     T* src = w.src.get((size_t)(c->n_t + 1) * N);
     for (int j = 0; j <= c->n_t; ++j)
@@ -483,6 +569,8 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
           adv<T>(c, y, vA, nullptr, nullptr, y, yh, acc, nullptr, 1, s1);
         }
         adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, y, nullptr, nullptr, 2, s2);
+        if (mtil)
+          REG_CUDA(cudaMemcpyAsync(mtil + (long)(j + 1) * N, y, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
       } else {
         const T* g1 = gm_slot<T>(c, j, base);
         const T* g2 = gmh_slot<T>(c, j + 1, base);
@@ -499,7 +587,8 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
   }
   // lam~_1 = -m~_1
   lincomb_t<T>((T)-1, y, (T)0, nullptr, y, N, c->s);
-  adjoint_solve<T>(c, vcoef, f);
+  if (c->hess == REG_HESS_NEWTON) newton_adjoint<T>(c, vcoef, wcoef, f);
+  else adjoint_solve<T>(c, vcoef, f);
 }
 
 }  // namespace
@@ -562,6 +651,10 @@ void prepare_mixed(reg_ctx* c) {
   const long dN = c->dN(), N = c->N();
   spectral<float>(c);
   convert<double, float>(c->vlin.p, x.vcoef.get(c->ncdN()), c->ncdN(), c->s);
+  if (c->hess == REG_HESS_NEWTON) {
+    convert<double, float>(w.m1.p, x.m1.get(N), N, c->s);
+    convert<double, float>(w.mR.p, x.mR.get(N), N, c->s);
+  }
   if (c->ckpt == 0) {
     convert<double, float>(w.gm.p, x.gm.get((size_t)(c->n_t + 1) * dN), (long)(c->n_t + 1) * dN, c->s);
     if (c->quad) convert<double, float>(w.gmh.p, x.gmh.get((size_t)(c->n_t + 1) * dN), (long)(c->n_t + 1) * dN, c->s);
@@ -576,6 +669,11 @@ void set_point(reg_ctx* c, const double* v) {
   c->ready = false;
   REG_CUDA(cudaMemcpyAsync(c->vlin.get(c->ncdN()), v, c->ncdN() * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
   state_solve_store<double>(c, c->vlin.p, c->mT.p);
+  if (c->hess == REG_HESS_NEWTON) {  // m_1 and m_R for the adjoint inside the Newton matvec
+    const long N = c->N();
+    REG_CUDA(cudaMemcpyAsync(c->w64.m1.get(N), c->w64.m.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    REG_CUDA(cudaMemcpyAsync(c->w64.mR.get(N), c->mR.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  }
 }
 
 void check_finite(double x, const char* what) {
@@ -621,7 +719,10 @@ size_t graph_signature(reg_ctx* c) {
                         c->w64.gmh.p,  c->w64.ck.p,   c->w32.U.p,    c->w32.W.p,    c->w32.X.p,    c->w32.m.p,
                         c->w32.yh.p,   c->w32.acc.p,  c->w32.lam.p,  c->w32.va.p,   c->w32.vb.p,   c->w32.wa.p,
                         c->w32.wb.p,   c->w32.gm.p,   c->w32.gmh.p,  c->w32.ck.p,   c->w32.vcoef.p, c->w32.wcoef.p,
-                        c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p,    c->w64.src.p,  c->w32.src.p};
+                        c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p,    c->w64.src.p,  c->w32.src.p,
+                        c->w64.mtil.p, c->w32.mtil.p, c->w64.lamN.p, c->w32.lamN.p, c->w64.yh2.p, c->w32.yh2.p,
+                        c->w64.acc2.p, c->w32.acc2.p, c->w64.st0.p,  c->w32.st0.p,  c->w64.st1.p,  c->w32.st1.p,
+                        c->w64.Gt.p,   c->w32.Gt.p};
   size_t h = 1469598103934665603ull;
   for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
   return h;
@@ -961,7 +1062,19 @@ reg_status reg_set_quadrature(reg_ctx* ctx, int quadrature) {
   API_BEGIN(ctx)
   if (quadrature != REG_QUAD_TRAPEZOID && quadrature != REG_QUAD_DISCRETE)
     throw StatusError{REG_EINVAL, "bad quadrature"};
+  if (quadrature == REG_QUAD_DISCRETE && c_->hess == REG_HESS_NEWTON)
+    throw StatusError{REG_EINVAL, "the full Newton Hessian uses the trapezoid quadrature"};
   c_->quad = quadrature;
+  c_->ready = false;
+  API_END
+}
+
+reg_status reg_set_hessian(reg_ctx* ctx, int kind) {
+  API_BEGIN(ctx)
+  if (kind != REG_HESS_GN && kind != REG_HESS_NEWTON) throw StatusError{REG_EINVAL, "bad Hessian kind"};
+  if (kind == REG_HESS_NEWTON && c_->quad != REG_QUAD_TRAPEZOID)
+    throw StatusError{REG_EINVAL, "the full Newton Hessian uses the trapezoid quadrature"};
+  c_->hess = kind;
   c_->ready = false;
   API_END
 }

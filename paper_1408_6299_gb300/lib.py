@@ -20,6 +20,7 @@ REG_ENONFINITE, REG_ECFL, REG_ELINESEARCH, REG_EMAXIT, REG_ETIMEOUT = 5, 6, 7, 8
 REG_H1, REG_H2 = 1, 2
 REG_FP64, REG_MIXED = 0, 1
 REG_QUAD_TRAPEZOID, REG_QUAD_DISCRETE = 0, 1
+REG_HESS_GN, REG_HESS_NEWTON = 0, 1
 
 _STATUS = {0: "REG_OK", 1: "REG_EINVAL", 2: "REG_ENOMEM", 3: "REG_ECUDA", 4: "REG_ENOTREADY",
            5: "REG_ENONFINITE", 6: "REG_ECFL", 7: "REG_ELINESEARCH", 8: "REG_EMAXIT", 9: "REG_ETIMEOUT"}
@@ -95,6 +96,7 @@ _SIGNATURES = {
                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "reg_destroy": [_vp],
     "reg_set_quadrature": [_vp, ctypes.c_int],
+    "reg_set_hessian": [_vp, ctypes.c_int],
     "reg_set_images": [_vp, _vp, _vp],
     "reg_objective": [_vp, _vp, _vp, _vp],
     "reg_gradient": [_vp, _vp, _vp, _vp],
@@ -216,7 +218,7 @@ class Registration:
     """One library context: grid, time discretisation and regulariser fixed at creation."""
 
     def __init__(self, n, n_t, n_c=1, beta=1e-2, reg=REG_H1, stokes=False, precision=REG_FP64, ckpt_every=0,
-                 stream=None, quadrature=REG_QUAD_TRAPEZOID):
+                 stream=None, quadrature=REG_QUAD_TRAPEZOID, hessian=REG_HESS_GN):
         self.L = load()
         self.n = tuple(int(k) for k in n)
         self.d = len(self.n)
@@ -230,6 +232,8 @@ class Registration:
         self.ctx = ctx
         if quadrature != REG_QUAD_TRAPEZOID:
             self._check(self.L.reg_set_quadrature(self.ctx, int(quadrature)))
+        if hessian != REG_HESS_GN:
+            self.set_hessian(hessian)
 
     @property
     def N(self):
@@ -254,6 +258,10 @@ class Registration:
             raise RegError(st, self.L.reg_last_error(self.ctx).decode())
 
     # each method passes raw pointers through; outputs are caller-allocated
+    def set_hessian(self, kind):
+        """REG_HESS_GN (default) or REG_HESS_NEWTON for hessvec and solve."""
+        self._check(self.L.reg_set_hessian(self.ctx, int(kind)))
+
     def set_images(self, mT, mR):
         a, ka = _addr(mT)
         b, kb = _addr(mR)

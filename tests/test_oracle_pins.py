@@ -590,3 +590,17 @@ def test_newton_is_the_gradient_derivative_at_second_order():
     assert np.all(np.abs(rates - 2) < 0.2), (errs_n, rates)
     assert errs_n[-1] < 1e-5
     assert min(errs_g) > 1e3 * errs_n[-1]  # the lambda terms are not negligible here
+
+
+def test_newton_solve_reaches_the_gauss_newton_minimiser():
+    # N-PCG (Sec. 4) and GN-PCG converge to the same stationary point (the
+    # gradient is pinned independently against finite differences of the
+    # objective); with the exact second derivative, no more outer iterations
+    c, P, mR = newton_setup(8)
+    vg, rg = P.solve(c["mT"], mR, grad_rtol=1e-6, max_outer=30)
+    vn, rn = P.solve(c["mT"], mR, grad_rtol=1e-6, max_outer=30, newton=True)
+    assert rg["status"] == 0 and rn["status"] == 0
+    assert rn["g_inf"] <= 1e-6 * rn["g0_inf"]
+    assert np.linalg.norm(vn - vg) <= 1e-5 * np.linalg.norm(vg)
+    assert rn["outer"] <= rg["outer"]
+    assert abs(rn["J"] - rg["J"]) <= 1e-9 * rg["J"]
