@@ -28,6 +28,7 @@
  *      (optimize-then-discretize, Sec. 3); a discrete-adjoint variant is kept
  *      for tests only.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -40,7 +41,9 @@
 #define ORC_OK 0
 #define ORC_EINVAL 1
 #define ORC_ENOMEM 2
+#define ORC_ECFL 6
 #define ORC_ELINESEARCH 7
+#define ORC_EMAXIT 8
 
 typedef struct {
   int d;         /* space dimension, 2 or 3 */
@@ -61,6 +64,11 @@ typedef struct {
   int max_backtracks;    /* line-search trials */
   int pcg_maxit;         /* 0: use n (order of the reduced system) */
   int newton;            /* 1: full Newton Hessian in PCG (N-PCG), else Gauss-Newton */
+  int picard;            /* 1: Picard / preconditioned gradient descent (Eq. picard) instead of PCG */
+  int step_memory;       /* 1: Picard step memory alpha~ (Sec. 3.3.5) */
+  int stop_rule;         /* 0: relative gradient; 1: the C1-C5 set (Eq. stopping-criteria) */
+  double tau_J;          /* tolerance of C1-C3 */
+  double cfl_max;        /* > 0: halve the step while CFL(v + s) exceeds it */
 } orc_opts;
 
 typedef struct {
@@ -73,6 +81,12 @@ typedef struct {
   double J0, J;       /* first and final objective */
   double g0_inf, g_inf;
   double g0_2, g_2;
+  int stop_flags;     /* bit i-1: criterion Ci held at exit (stop_rule 1) */
+  int cfl_halvings;   /* step halvings forced by cfl_max */
+  double alpha_mem;   /* final Picard step memory alpha~ */
+  double J_prev;      /* objective of the previous iterate */
+  double dv_inf;      /* ||v_{k-1} - v_k||_inf of the last step */
+  double v_inf;       /* ||v_k||_inf */
 } orc_report;
 
 /* ------------------------------------------------------------------ */
@@ -1053,8 +1067,44 @@ static double norm_inf(long n, const double *a) {
   return s;
 }
 
+/* Termination test at iterate k (Eq. stopping-criteria / Eq. converged, or
+ * the relative gradient reduction of Sec. 3.3.5). Returns 1 to stop; *flags
+ * gets the criteria that hold; *maxed is set when only the iteration cap
+ * stops the solve. */
+static int stop_test(const orc_opts *O, const orc_report *R, int k, double ginf, int *flags, int *maxed) {
+  *flags = 0;
+  *maxed = 0;
+  if (O->stop_rule == 0) {
+    if (ginf <= O->grad_rtol * R->g0_inf) return 1;
+    if (k >= O->max_outer) {
+      *maxed = 1;
+      return 1;
+    }
+    return 0;
+  }
+  double tau = O->tau_J, one_J0 = 1.0 + R->J0;
+  if (k >= 1 && R->J_prev - R->J < tau * one_J0) *flags |= 1;          /* C1 */
+  if (k >= 1 && R->dv_inf < sqrt(tau) * (1.0 + R->v_inf)) *flags |= 2; /* C2 */
+  if (ginf < cbrt(tau) * one_J0) *flags |= 4;                          /* C3 */
+  if (ginf < 1e3 * DBL_EPSILON) *flags |= 8;                           /* C4 */
+  if (k > O->max_outer) *flags |= 16;                                  /* C5 */
+  int conv = ((*flags & 7) == 7) || (*flags & 8);
+  if (conv) return 1;
+  if (*flags & 16) {
+    *maxed = 1;
+    return 1;
+  }
+  return 0;
+}
+
+/* Outer loop (Alg. 1): the search direction is the inexact (G)N step from
+ * PCG on H s = -g (Nocedal & Wright Alg. 5.3) or, with opts.picard, the
+ * Picard update s = -P^{-1} g (Eq. picard; App. C: the difference between the
+ * Picard iterate -(beta C (x) A)^{-1} K f and v_k), scaled by the step memory
+ * alpha~; then CFL halving and Armijo backtracking from alpha = 1. */
 int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const double *mR, double *v, orc_report *R) {
   if (!prob_ok(P)) return ORC_EINVAL;
+  if (O->newton && P->dto) return ORC_EINVAL;
   long N = grid_N(P);
   long n = (long)P->n_c * P->d * N;
   double hd = cell_volume(P);
@@ -1066,52 +1116,75 @@ int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const doub
   int st = (!g || !s || !r || !z || !p || !Hp || !vtrial) ? ORC_ENOMEM : 0;
   double J = 0.0, out3[3];
   long maxit = O->pcg_maxit > 0 ? O->pcg_maxit : n;
+  double amem = 1.0;
+  R->alpha_mem = amem;
   if (!st) st = orc_gradient(P, v, mT, mR, g, &J);
   R->n_pde += 2;
   if (!st) {
     R->J0 = J;
     R->g0_inf = norm_inf(n, g);
     R->g0_2 = sqrt(dot(n, g, g));
+    R->v_inf = norm_inf(n, v);
   }
-  int k = 0;
+  int k = 0, maxed = 0;
   while (!st) {
     double ginf = norm_inf(n, g), g2 = sqrt(dot(n, g, g));
     R->g_inf = ginf;
     R->g_2 = g2;
     R->J = J;
-    if (ginf <= O->grad_rtol * R->g0_inf || k >= O->max_outer) break;
-    /* PCG on H s = -g from s = 0 (Nocedal & Wright Alg. 5.3) */
-    double eta = fmin(0.5, sqrt(g2 / R->g0_2));
-    memset(s, 0, sizeof(double) * n);
-    memcpy(r, g, sizeof(double) * n); /* r_0 = H s_0 + g = g */
-    st = orc_precond(P, r, z);
-    for (long q = 0; q < n && !st; ++q) p[q] = -z[q];
-    double rz = dot(n, r, z);
-    for (long it = 0; it < maxit && !st; ++it) {
-      if (sqrt(dot(n, r, r)) <= eta * g2) break;
-      st = O->newton ? orc_hessvec_newton(P, v, mT, mR, p, Hp) : orc_hessvec(P, v, mT, p, Hp);
-      R->matvecs += 1;
-      R->n_pde += 2;
-      R->pcg_iters += 1;
+    if (stop_test(O, R, k, ginf, &R->stop_flags, &maxed)) break;
+    if (O->picard) {
+      st = orc_precond(P, g, s);
       if (st) break;
-      double pHp = dot(n, p, Hp);
-      if (pHp <= 0.0) {
-        if (it == 0) memcpy(s, p, sizeof(double) * n);
-        break;
-      }
-      double alpha = rz / pHp;
-      for (long q = 0; q < n; ++q) {
-        s[q] += alpha * p[q];
-        r[q] += alpha * Hp[q];
-      }
+      double sc = O->step_memory ? -amem : -1.0;
+      for (long q = 0; q < n; ++q) s[q] *= sc;
+    } else {
+      /* PCG on H s = -g from s = 0 */
+      double eta = fmin(0.5, sqrt(g2 / R->g0_2));
+      memset(s, 0, sizeof(double) * n);
+      memcpy(r, g, sizeof(double) * n); /* r_0 = H s_0 + g = g */
       st = orc_precond(P, r, z);
+      for (long q = 0; q < n && !st; ++q) p[q] = -z[q];
+      double rz = dot(n, r, z);
+      for (long it = 0; it < maxit && !st; ++it) {
+        if (sqrt(dot(n, r, r)) <= eta * g2) break;
+        st = O->newton ? orc_hessvec_newton(P, v, mT, mR, p, Hp) : orc_hessvec(P, v, mT, p, Hp);
+        R->matvecs += 1;
+        R->n_pde += 2;
+        R->pcg_iters += 1;
+        if (st) break;
+        double pHp = dot(n, p, Hp);
+        if (pHp <= 0.0) {
+          if (it == 0) memcpy(s, p, sizeof(double) * n);
+          break;
+        }
+        double alpha = rz / pHp;
+        for (long q = 0; q < n; ++q) {
+          s[q] += alpha * p[q];
+          r[q] += alpha * Hp[q];
+        }
+        st = orc_precond(P, r, z);
+        if (st) break;
+        double rz_new = dot(n, r, z);
+        double bta = rz_new / rz;
+        rz = rz_new;
+        for (long q = 0; q < n; ++q) p[q] = -z[q] + bta * p[q];
+      }
       if (st) break;
-      double rz_new = dot(n, r, z);
-      double bta = rz_new / rz;
-      rz = rz_new;
-      for (long q = 0; q < n; ++q) p[q] = -z[q] + bta * p[q];
     }
-    if (st) break;
+    /* keep v + s inside the CFL bound by halving s (Sec. 3.3.5) */
+    if (O->cfl_max > 0.0) {
+      for (;;) {
+        for (long q = 0; q < n; ++q) vtrial[q] = v[q] + s[q];
+        if (orc_cfl(P, vtrial) <= O->cfl_max) break;
+        if (++R->cfl_halvings > 30) {
+          st = ORC_ECFL;
+          break;
+        }
+        for (long q = 0; q < n; ++q) s[q] *= 0.5;
+      }
+      if (st) break;
+    }
     /* Armijo backtracking from alpha = 1 */
     double slope = hd * dot(n, g, s);
     double alpha = 1.0, Jt = 0.0;
@@ -1134,12 +1207,21 @@ int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const doub
       st = ORC_ELINESEARCH;
       break;
     }
+    /* step memory: double after a full step, else scale by the accepted alpha */
+    if (O->picard && O->step_memory) amem = (alpha == 1.0) ? 2.0 * amem : amem * alpha;
+    R->alpha_mem = amem;
+    double dv = 0.0;
+    for (long q = 0; q < n; ++q) dv = fmax(dv, fabs(vtrial[q] - v[q]));
     memcpy(v, vtrial, sizeof(double) * n);
+    R->dv_inf = dv;
+    R->v_inf = norm_inf(n, v);
+    R->J_prev = J;
     st = orc_gradient(P, v, mT, mR, g, &J);
     R->n_pde += 2;
     k += 1;
   }
   R->outer = k;
+  if (!st && maxed) st = ORC_EMAXIT;
   R->status = st;
   free(g); free(s); free(r); free(z); free(p); free(Hp); free(vtrial);
   return st;

@@ -47,6 +47,11 @@ class Opts(ctypes.Structure):
         ("max_backtracks", ctypes.c_int),
         ("pcg_maxit", ctypes.c_int),
         ("newton", ctypes.c_int),
+        ("picard", ctypes.c_int),
+        ("step_memory", ctypes.c_int),
+        ("stop_rule", ctypes.c_int),
+        ("tau_J", ctypes.c_double),
+        ("cfl_max", ctypes.c_double),
     ]
 
 
@@ -64,6 +69,12 @@ class Report(ctypes.Structure):
         ("g_inf", ctypes.c_double),
         ("g0_2", ctypes.c_double),
         ("g_2", ctypes.c_double),
+        ("stop_flags", ctypes.c_int),
+        ("cfl_halvings", ctypes.c_int),
+        ("alpha_mem", ctypes.c_double),
+        ("J_prev", ctypes.c_double),
+        ("dv_inf", ctypes.c_double),
+        ("v_inf", ctypes.c_double),
     ]
 
 
@@ -251,11 +262,15 @@ class Problem:
         return float(lib().orc_cfl(ctypes.byref(self._p), _ptr(v)))
 
     def solve(self, mT, mR, v0=None, grad_rtol=1e-2, max_outer=50, armijo_c1=1e-4, backtrack=0.5,
-              max_backtracks=20, pcg_maxit=0, newton=False):
+              max_backtracks=20, pcg_maxit=0, newton=False, picard=False, step_memory=True, stop_rule=0,
+              tau_J=1e-3, cfl_max=0.0):
+        """Outer solve (Alg. 1). Returns (v, report dict); report["status"] is
+        0, 6 (CFL halvings exhausted), 7 (line search failed) or 8 (iteration cap)."""
         v = np.zeros(self.coef_shape()) if v0 is None else _f64(v0).reshape(self.coef_shape()).copy()
         if newton and self.dto:
             raise ValueError("the full Newton Hessian uses the trapezoid quadrature")
-        opts = Opts(grad_rtol, max_outer, armijo_c1, backtrack, max_backtracks, pcg_maxit, int(bool(newton)))
+        opts = Opts(grad_rtol, max_outer, armijo_c1, backtrack, max_backtracks, pcg_maxit, int(bool(newton)),
+                    int(bool(picard)), int(bool(step_memory)), int(stop_rule), float(tau_J), float(cfl_max))
         rep = Report()
         st = lib().orc_solve(ctypes.byref(self._p), ctypes.byref(opts), _ptr(_f64(mT)), _ptr(_f64(mR)),
                              _ptr(v), ctypes.byref(rep))

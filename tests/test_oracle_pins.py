@@ -604,3 +604,86 @@ def test_newton_solve_reaches_the_gauss_newton_minimiser():
     assert np.linalg.norm(vn - vg) <= 1e-5 * np.linalg.norm(vg)
     assert rn["outer"] <= rg["outer"]
     assert abs(rn["J"] - rg["J"]) <= 1e-9 * rg["J"]
+
+
+# ---------------------------------------------------------------------------
+# Picard / preconditioned gradient descent (Eq. picard, App. C), the step
+# memory alpha~ and the C1-C5 stopping set (Sec. 3.3.5, Eq. stopping-criteria)
+# ---------------------------------------------------------------------------
+
+def numpy_picard_first_iterate(P, mT, mR):
+    # Eq. picard at v = 0 for H1, no Stokes, n_c = 1: the state is m_T at all
+    # times and the adjoint is m_R - m_T, so f = (m_R - m_T) grad m_T and
+    # v_1 = -(beta A)^{-1} f, with A = -Lap and its k = 0 mode scaled by one
+    n = P.n
+    ks = [np.fft.fftfreq(k, 1.0 / k) for k in n]
+    K = np.meshgrid(*ks, indexing="ij")
+    mh = np.fft.fftn(mT)
+    f = []
+    for i, k in enumerate(n):
+        kt = K[i].copy()
+        kt[np.abs(kt) == k // 2] = 0  # Nyquist-masked first derivative
+        f.append((mR - mT) * np.real(np.fft.ifftn(1j * kt * mh)))
+    k2 = sum(k * k for k in K)
+    a = P.beta * k2
+    a[k2 == 0] = 1.0
+    return np.stack([-np.real(np.fft.ifftn(np.fft.fftn(fi) / a)) for fi in f])[None]
+
+
+def picard_problem():
+    c = synth.sinusoid_2d(32)
+    P = O.Problem(c["n"], 8, 1, c["beta"], 1, False)
+    mR = O.Problem(c["n"], 16).state(c["v_true"], c["mT"])[-1]
+    return c, P, mR
+
+
+def test_picard_first_step_is_the_picard_iterate():
+    c, P, mR = picard_problem()
+    v1, rep = P.solve(c["mT"], mR, max_outer=1, picard=True, step_memory=False)
+    ref = numpy_picard_first_iterate(P, c["mT"], mR)
+    alpha = 0.5 ** (rep["ls_trials"] - 1)  # Armijo halvings from alpha = 1
+    assert rep["outer"] == 1 and rep["pcg_iters"] == 0
+    assert np.abs(v1 - alpha * ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_picard_step_memory_rule():
+    # alpha~ doubles after a full step and is scaled by the accepted alpha otherwise
+    c, P, mR = picard_problem()
+    amem, trials = 1.0, 0
+    for k in range(1, 9):
+        _, rep = P.solve(c["mT"], mR, max_outer=k, picard=True)
+        t = rep["ls_trials"] - trials
+        trials = rep["ls_trials"]
+        amem = 2 * amem if t == 1 else amem * 0.5 ** (t - 1)
+        assert rep["alpha_mem"] == amem, k
+
+
+def test_picard_reaches_the_newton_krylov_minimiser():
+    c, P, mR = picard_problem()
+    vg, rg = P.solve(c["mT"], mR, grad_rtol=1e-8, max_outer=30)
+    vp, rp = P.solve(c["mT"], mR, grad_rtol=1e-5, max_outer=2000, picard=True)
+    assert rp["status"] == 0 and rp["g_inf"] <= 1e-5 * rp["g0_inf"]
+    assert np.linalg.norm(vp - vg) <= 2e-4 * np.linalg.norm(vg)  # linear convergence: ~10x the gradient tolerance
+    assert rp["outer"] > 3 * rg["outer"]  # first order: many more outer iterations (Sec. 5.2)
+
+
+def test_stopping_set_c1_to_c5():
+    c, P, mR = picard_problem()
+    for kw in (dict(), dict(picard=True), dict(newton=True)):
+        v, rep = P.solve(c["mT"], mR, stop_rule=1, tau_J=1e-3, max_outer=100, **kw)
+        assert rep["status"] == 0
+        tau, J0 = 1e-3, rep["J0"]
+        flags = ((rep["J_prev"] - rep["J"] < tau * (1 + J0)) * 1 + (rep["dv_inf"] < tau ** 0.5 * (1 + rep["v_inf"])) * 2
+                 + (rep["g_inf"] < tau ** (1 / 3) * (1 + J0)) * 4 + (rep["g_inf"] < 1e3 * np.finfo(float).eps) * 8)
+        assert rep["stop_flags"] == flags and (flags & 7) == 7, kw
+        # one iterate earlier the set did not hold: capped there, C5 stops the solve
+        K = rep["outer"]
+        _, r2 = P.solve(c["mT"], mR, stop_rule=1, tau_J=1e-3, max_outer=K - 2, **kw)
+        assert r2["status"] == 8 and r2["outer"] == K - 1 and (r2["stop_flags"] & 7) != 7 and r2["stop_flags"] & 16
+
+
+def test_stopping_set_c4_at_a_stationary_start():
+    # m_R = m_T and v_0 = 0: the gradient vanishes identically, C4 stops at k = 0
+    c, P, _ = picard_problem()
+    v, rep = P.solve(c["mT"], c["mT"], stop_rule=1)
+    assert rep["status"] == 0 and rep["outer"] == 0 and rep["stop_flags"] & 8 and rep["g_inf"] == 0.0
