@@ -201,7 +201,23 @@ typedef struct {
   long pcg_maxit;       /* 0 = order of the reduced system (Sec. 3.3.5) */
   double cfl_max;       /* > 0: halve the step while the CFL number of v+s exceeds it (Sec. 3.3.5) */
   int detF_substeps;    /* > 0: compute det F_1 statistics at the end with this many substeps */
+  int method;           /* REG_METHOD_KRYLOV (PCG with the context's Hessian) or REG_METHOD_PICARD */
+  int step_memory;      /* Picard: 1 = scale the step by alpha~, doubled after a full step and
+                           multiplied by the accepted alpha otherwise (Sec. 3.3.5); default 1 */
+  int stop_rule;        /* REG_STOP_GRAD_REL (grad_rtol) or REG_STOP_C1C5 (Eq. stopping-criteria) */
+  double tau_J;         /* tolerance tau_J of C1-C3 (1e-3, Sec. 3.3.5) */
 } reg_solve_opts;
+
+enum {
+  REG_METHOD_KRYLOV = 0, /* inexact (Gauss-)Newton-Krylov: PCG on H s = -g (Alg. 1) */
+  REG_METHOD_PICARD = 1  /* Picard iteration / preconditioned gradient descent: s = -P^{-1} g,
+                            the difference between the iterate of Eq. picard and v_k (App. C) */
+};
+enum {
+  REG_STOP_GRAD_REL = 0, /* stop at ||g_k||_inf <= grad_rtol ||g_0||_inf; REG_EMAXIT at k = max_outer */
+  REG_STOP_C1C5 = 1      /* stop on (C1 and C2 and C3) or C4 (Eq. converged); C5 (k > max_outer)
+                            stops with REG_EMAXIT */
+};
 
 typedef struct {
   int outer;            /* outer iterations k* */
@@ -217,15 +233,25 @@ typedef struct {
   double cfl;           /* CFL number of the final v */
   double detF[4];       /* min, max, mean, std of det F_1 (if requested) */
   double seconds;       /* wall time of the solve */
+  int stop_flags;       /* REG_STOP_C1C5: bit i-1 set when criterion Ci held at exit */
+  double alpha_mem;     /* final Picard step memory alpha~ (1 otherwise) */
+  double J_prev;        /* objective of the previous iterate (C1) */
+  double dv_inf;        /* ||v_{k-1} - v_k||_inf of the last step (C2) */
+  double v_inf;         /* ||v_k||_inf of the final iterate (C2) */
 } reg_solve_report;
 
-/* Fill opts with the defaults above (grad_rtol 1e-2, max_outer 50). */
+/* Fill opts with the defaults above (grad_rtol 1e-2, max_outer 50, Krylov
+ * method, relative-gradient stop, step memory on, tau_J 1e-3). */
 REG_API void reg_solve_opts_default(reg_solve_opts* opts);
 
-/* Inexact Gauss-Newton-Krylov solve (Alg. 1): PCG with the forcing term
- * eta_k = min(0.5, sqrt(||g_k||_2/||g_0||_2)) (Eq. termination-criterion-ksm),
- * preconditioner reg_precond, Armijo backtracking from alpha = 1. v_inout:
- * initial guess in, solution out (n_c*d*N). report (may be NULL): host. */
+/* Outer solve (Alg. 1). REG_METHOD_KRYLOV: inexact Newton-Krylov with PCG,
+ * forcing term eta_k = min(0.5, sqrt(||g_k||_2/||g_0||_2)) (Eq.
+ * termination-criterion-ksm), preconditioner reg_precond, the Hessian chosen
+ * by reg_set_hessian (GN-PCG or N-PCG). REG_METHOD_PICARD: s = -P^{-1} g
+ * (Eq. picard) with the optional step memory. Then CFL halving (cfl_max) and
+ * Armijo backtracking from alpha = 1. v_inout: initial guess in, solution out
+ * (n_c*d*N). report (may be NULL): host. Returns REG_EMAXIT when the
+ * iteration cap ends the solve (v_inout holds the last iterate). */
 REG_API reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report);
 
 /* One independent registration problem of a batch (Sec. 1.1 for each pair).

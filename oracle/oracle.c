@@ -1174,14 +1174,15 @@ int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const doub
     }
     /* keep v + s inside the CFL bound by halving s (Sec. 3.3.5) */
     if (O->cfl_max > 0.0) {
-      for (;;) {
+      for (int halvings = 0;; ++halvings) {
         for (long q = 0; q < n; ++q) vtrial[q] = v[q] + s[q];
         if (orc_cfl(P, vtrial) <= O->cfl_max) break;
-        if (++R->cfl_halvings > 30) {
+        if (halvings == 30) { /* 30 halvings of this step did not suffice */
           st = ORC_ECFL;
           break;
         }
         for (long q = 0; q < n; ++q) s[q] *= 0.5;
+        R->cfl_halvings += 1;
       }
       if (st) break;
     }

@@ -10,6 +10,7 @@
 // (ckpt_every = K). The body-force time integral uses the trapezoid rule on
 // the nodes (default) or the stage values of the discrete adjoint.
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -844,11 +845,43 @@ void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_o
 }
 
 // ---------------------------------------------------------------------------
-// Alg. 1: inexact Gauss-Newton-Krylov with PCG (Nocedal & Wright Alg. 5.3),
-// forcing term Eq. termination-criterion-ksm, Armijo backtracking.
+// Termination test at iterate k: the relative gradient reduction, or the set
+// C1-C5 of Eq. stopping-criteria combined as in Eq. converged. Returns true to
+// stop; maxed is set when only the iteration cap stops the solve.
+// ---------------------------------------------------------------------------
+bool stop_test(const reg_solve_opts& o, reg_solve_report& R, int k, double ginf, bool& maxed) {
+  maxed = false;
+  R.stop_flags = 0;
+  if (o.stop_rule == REG_STOP_GRAD_REL) {
+    if (ginf <= o.grad_rtol * R.g0_inf) return true;
+    maxed = k >= o.max_outer;
+    return maxed;
+  }
+  const double tau = o.tau_J, one_J0 = 1.0 + R.J0;
+  int f = 0;
+  if (k >= 1 && R.J_prev - R.J < tau * one_J0) f |= 1;             // C1
+  if (k >= 1 && R.dv_inf < std::sqrt(tau) * (1.0 + R.v_inf)) f |= 2; // C2
+  if (ginf < std::cbrt(tau) * one_J0) f |= 4;                       // C3
+  if (ginf < 1e3 * DBL_EPSILON) f |= 8;                             // C4
+  if (k > o.max_outer) f |= 16;                                     // C5
+  R.stop_flags = f;
+  if ((f & 7) == 7 || (f & 8)) return true;
+  maxed = (f & 16) != 0;
+  return maxed;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 1: the outer loop. Search direction: the inexact (Gauss-)Newton step
+// from PCG (Nocedal & Wright Alg. 5.3) with the forcing term of Eq.
+// termination-criterion-ksm, or the Picard update -P^{-1} g (Eq. picard,
+// App. C) scaled by the step memory alpha~; then CFL halving and Armijo
+// backtracking.
 // ---------------------------------------------------------------------------
 int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
   auto t0 = std::chrono::steady_clock::now();
+  if (o.method != REG_METHOD_KRYLOV && o.method != REG_METHOD_PICARD) throw StatusError{REG_EINVAL, "bad method"};
+  if (o.stop_rule != REG_STOP_GRAD_REL && o.stop_rule != REG_STOP_C1C5) throw StatusError{REG_EINVAL, "bad stop_rule"};
+  if (o.stop_rule == REG_STOP_C1C5 && !(o.tau_J > 0.0)) throw StatusError{REG_EINVAL, "tau_J must be positive"};
   const long n = c->ncdN();
   double* g = c->sv_g.get(n);
   double* s = c->sv_s.get(n);
@@ -865,6 +898,9 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
   double J = parts[0] + parts[1];
   R.J0 = J;
   R.g0_inf = maxabs(g, n, rs, c->s);
+  R.v_inf = maxabs(v, n, rs, c->s);
+  double amem = 1.0;
+  R.alpha_mem = amem;
   double g0_2 = std::sqrt(dot(g, g, n, rs, c->s));
   long maxit = o.pcg_maxit > 0 ? o.pcg_maxit : n;
   int status = REG_OK;
@@ -874,40 +910,45 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
     double g2 = std::sqrt(dot(g, g, n, rs, c->s));
     R.g_inf = ginf;
     R.J = J;
-    if (ginf <= o.grad_rtol * R.g0_inf) break;
-    if (k >= o.max_outer) {
-      status = REG_EMAXIT;
+    bool maxed = false;
+    if (stop_test(o, R, k, ginf, maxed)) {
+      if (maxed) status = REG_EMAXIT;
       break;
     }
-    double eta = std::min(0.5, std::sqrt(g2 / g0_2));
-    // PCG on H s = -g from s = 0
-    REG_CUDA(cudaMemsetAsync(s, 0, n * sizeof(double), c->s));
-    REG_CUDA(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
-    precond(c, r, z);
-    lincomb(-1.0, z, 0.0, z, p, n, c->s);
-    double rz = dot(r, z, n, rs, c->s);
-    for (long it = 0; it < maxit; ++it) {
-      double rn = std::sqrt(dot(r, r, n, rs, c->s));
-      check_finite(rn, "PCG residual");
-      if (rn <= eta * g2) break;
-      hessvec(c, p, Hp);
-      R.matvecs += 1;
-      R.n_pde += 2;
-      R.pcg_iters += 1;
-      double pHp = dot(p, Hp, n, rs, c->s);
-      check_finite(pHp, "PCG curvature");
-      if (pHp <= 0.0) {
-        if (it == 0) REG_CUDA(cudaMemcpyAsync(s, p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
-        break;
-      }
-      double alpha = rz / pHp;
-      axpby(alpha, p, 1.0, s, n, c->s);
-      axpby(alpha, Hp, 1.0, r, n, c->s);
+    if (o.method == REG_METHOD_PICARD) {
+      precond(c, g, s);
+      axpby(0.0, s, o.step_memory ? -amem : -1.0, s, n, c->s);
+    } else {
+      double eta = std::min(0.5, std::sqrt(g2 / g0_2));
+      // PCG on H s = -g from s = 0
+      REG_CUDA(cudaMemsetAsync(s, 0, n * sizeof(double), c->s));
+      REG_CUDA(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
       precond(c, r, z);
-      double rz_new = dot(r, z, n, rs, c->s);
-      double bta = rz_new / rz;
-      rz = rz_new;
-      axpby(-1.0, z, bta, p, n, c->s);
+      lincomb(-1.0, z, 0.0, z, p, n, c->s);
+      double rz = dot(r, z, n, rs, c->s);
+      for (long it = 0; it < maxit; ++it) {
+        double rn = std::sqrt(dot(r, r, n, rs, c->s));
+        check_finite(rn, "PCG residual");
+        if (rn <= eta * g2) break;
+        hessvec(c, p, Hp);
+        R.matvecs += 1;
+        R.n_pde += 2;
+        R.pcg_iters += 1;
+        double pHp = dot(p, Hp, n, rs, c->s);
+        check_finite(pHp, "PCG curvature");
+        if (pHp <= 0.0) {
+          if (it == 0) REG_CUDA(cudaMemcpyAsync(s, p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+          break;
+        }
+        double alpha = rz / pHp;
+        axpby(alpha, p, 1.0, s, n, c->s);
+        axpby(alpha, Hp, 1.0, r, n, c->s);
+        precond(c, r, z);
+        double rz_new = dot(r, z, n, rs, c->s);
+        double bta = rz_new / rz;
+        rz = rz_new;
+        axpby(-1.0, z, bta, p, n, c->s);
+      }
     }
     // keep the step inside the CFL bound by halving it (Sec. 3.3.5)
     if (o.cfl_max > 0) {
@@ -941,7 +982,14 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
       status = REG_ELINESEARCH;
       break;
     }
+    // step memory: doubled after a full step, else scaled by the accepted alpha
+    if (o.method == REG_METHOD_PICARD && o.step_memory) amem = (alpha == 1.0) ? 2.0 * amem : amem * alpha;
+    R.alpha_mem = amem;
+    lincomb(1.0, vt, -1.0, v, r, n, c->s);  // v_k - v_{k-1}
+    R.dv_inf = maxabs(r, n, rs, c->s);
     REG_CUDA(cudaMemcpyAsync(v, vt, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    R.v_inf = maxabs(v, n, rs, c->s);
+    R.J_prev = J;
     gradient(c, v, g, parts);
     R.n_pde += 2;
     J = parts[0] + parts[1];
@@ -1258,6 +1306,10 @@ void reg_solve_opts_default(reg_solve_opts* o) {
   o->pcg_maxit = 0;
   o->cfl_max = 0.0;
   o->detF_substeps = 0;
+  o->method = REG_METHOD_KRYLOV;
+  o->step_memory = 1;
+  o->stop_rule = REG_STOP_GRAD_REL;
+  o->tau_J = 1e-3;
 }
 
 reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report) {

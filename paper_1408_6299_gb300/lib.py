@@ -21,6 +21,8 @@ REG_H1, REG_H2 = 1, 2
 REG_FP64, REG_MIXED = 0, 1
 REG_QUAD_TRAPEZOID, REG_QUAD_DISCRETE = 0, 1
 REG_HESS_GN, REG_HESS_NEWTON = 0, 1
+REG_METHOD_KRYLOV, REG_METHOD_PICARD = 0, 1
+REG_STOP_GRAD_REL, REG_STOP_C1C5 = 0, 1
 
 _STATUS = {0: "REG_OK", 1: "REG_EINVAL", 2: "REG_ENOMEM", 3: "REG_ECUDA", 4: "REG_ENOTREADY",
            5: "REG_ENONFINITE", 6: "REG_ECFL", 7: "REG_ELINESEARCH", 8: "REG_EMAXIT", 9: "REG_ETIMEOUT"}
@@ -36,7 +38,23 @@ class SolveOpts(ctypes.Structure):
         ("pcg_maxit", ctypes.c_long),
         ("cfl_max", ctypes.c_double),
         ("detF_substeps", ctypes.c_int),
+        ("method", ctypes.c_int),
+        ("step_memory", ctypes.c_int),
+        ("stop_rule", ctypes.c_int),
+        ("tau_J", ctypes.c_double),
     ]
+
+    @classmethod
+    def make(cls, L, opts):
+        """Library defaults overridden by the keyword options (unknown names raise)."""
+        o = cls()
+        L.reg_solve_opts_default(ctypes.byref(o))
+        names = {f for f, _ in cls._fields_}
+        for k, val in opts.items():
+            if k not in names:
+                raise TypeError(f"unknown solve option {k!r}")
+            setattr(o, k, val)
+        return o
 
 
 class SolveReport(ctypes.Structure):
@@ -56,6 +74,11 @@ class SolveReport(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("detF", ctypes.c_double * 4),
         ("seconds", ctypes.c_double),
+        ("stop_flags", ctypes.c_int),
+        ("alpha_mem", ctypes.c_double),
+        ("J_prev", ctypes.c_double),
+        ("dv_inf", ctypes.c_double),
+        ("v_inf", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -157,10 +180,7 @@ def solve_batched(problems, precision=REG_MIXED, workers=8, **opts):
         arr[i] = ProblemC(len(n), (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))), int(p["n_t"]),
                           int(p.get("n_c", 1)), float(p["beta"]), int(p.get("reg", REG_H1)),
                           int(bool(p.get("stokes", False))), a, b, c)
-    o = SolveOpts()
-    L.reg_solve_opts_default(ctypes.byref(o))
-    for k, val in opts.items():
-        setattr(o, k, val)
+    o = SolveOpts.make(L, opts)
     reps = (SolveReport * len(problems))()
     st = L.reg_solve_batched(arr, len(problems), int(precision), ctypes.byref(o), reps, int(workers))
     if st not in (REG_OK, REG_EMAXIT):
@@ -339,10 +359,7 @@ class Registration:
 
     def solve(self, v, **opts):
         """Solve in place on v; returns the report dict (raises on a failed solve)."""
-        o = SolveOpts()
-        self.L.reg_solve_opts_default(ctypes.byref(o))
-        for k, val in opts.items():
-            setattr(o, k, val)
+        o = SolveOpts.make(self.L, opts)
         a, ka = _addr(v)
         rep = SolveReport()
         st = self.L.reg_solve(self.ctx, a, ctypes.byref(o), ctypes.byref(rep))

@@ -42,3 +42,29 @@ def test_create_without_device_fails_cleanly():
     except lib.RegError as e:
         with_err = e
     assert with_err is not None and with_err.status in (lib.REG_ECUDA, lib.REG_ENOMEM)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of the header's structs: same size and field offsets
+    import subprocess
+    structs = {"reg_solve_opts": lib.SolveOpts, "reg_solve_report": lib.SolveReport, "reg_problem": lib.ProblemC}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "reg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, f, val = line.split()
+            got[(cname, f)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
