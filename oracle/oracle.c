@@ -956,7 +956,7 @@ int orc_hessvec_newton(const orc_prob *P, const double *v, const double *mT, con
 
 /* dF/dt = -(v . grad) F + (grad v) F, F_0 = I, Heun in time;
  * (grad v)_{ik} = d v_i / d x_k. detF: N values of det F_1. */
-int orc_detF(const orc_prob *P, const double *v, double *detF) {
+static int defgrad(const orc_prob *P, const double *v, double *Fout, double *detF) {
   if (!prob_ok(P)) return ORC_EINVAL;
   long N = grid_N(P);
   int d = P->d, nt = P->n_t, nc = P->n_c, dd = d * d;
@@ -1013,7 +1013,8 @@ int orc_detF(const orc_prob *P, const double *v, double *detF) {
       }
     }
   }
-  if (!st) {
+  if (!st && Fout) memcpy(Fout, F, sizeof(double) * dd * N);
+  if (!st && detF) {
 #pragma omp parallel for schedule(static)
     for (long x = 0; x < N; ++x) {
       if (d == 2) {
@@ -1027,6 +1028,115 @@ int orc_detF(const orc_prob *P, const double *v, double *detF) {
     }
   }
   free(gv); free(F); free(Fh); free(K1); free(K2); free(vt); free(gt); free(Gt); free(k);
+  return st;
+}
+
+int orc_detF(const orc_prob *P, const double *v, double *detF) { return defgrad(P, v, NULL, detF); }
+
+/* F_1 itself: d*d fields, F[(a*d + c)*N + x] = F_ac */
+int orc_defgrad(const orc_prob *P, const double *v, double *F) { return defgrad(P, v, F, NULL); }
+
+/* Grid-angle measure of the deformation (Sec. 3.3.5 "Regularization", the
+ * acute angle of a deformed grid element): the edges e_c of a cell map to the
+ * columns F_1 e_c; per point, the smallest over column pairs of
+ * min(theta, pi - theta), theta the angle between the two columns. angle: N
+ * values in [0, pi/2]; pi/2 for F = I. */
+int orc_grid_angle(const orc_prob *P, const double *v, double *angle) {
+  if (!prob_ok(P)) return ORC_EINVAL;
+  long N = grid_N(P);
+  int d = P->d;
+  double *F = malloc(sizeof(double) * d * d * N);
+  if (!F) return ORC_ENOMEM;
+  int st = defgrad(P, v, F, NULL);
+  if (!st) {
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < N; ++x) {
+      double best = 0.5 * M_PI;
+      for (int c1 = 0; c1 < d; ++c1)
+        for (int c2 = c1 + 1; c2 < d; ++c2) {
+          double dot12 = 0.0, n1 = 0.0, n2 = 0.0;
+          for (int a = 0; a < d; ++a) {
+            double f1 = F[(a * d + c1) * N + x], f2 = F[(a * d + c2) * N + x];
+            dot12 += f1 * f2;
+            n1 += f1 * f1;
+            n2 += f2 * f2;
+          }
+          double cs = dot12 / sqrt(n1 * n2);
+          if (cs > 1.0) cs = 1.0;
+          if (cs < -1.0) cs = -1.0;
+          double th = acos(cs);
+          double acute = th < 0.5 * M_PI ? th : M_PI - th;
+          if (acute < best) best = acute;
+        }
+      angle[x] = best;
+    }
+  }
+  free(F);
+  return st;
+}
+
+/* Deformation map (App. D Eq. displacement): du/dt + (grad u) v = v, u_0 = 0,
+ * componentwise du_i/dt = -v . grad u_i + v_i, Heun steps on the time nodes
+ * as the state equation. u: d fields, the displacement u_1 (y = x - u_1). */
+int orc_displacement(const orc_prob *P, const double *v, double *u) {
+  if (!prob_ok(P)) return ORC_EINVAL;
+  long N = grid_N(P);
+  int d = P->d, nt = P->n_t;
+  double h = 1.0 / nt;
+  double *va = malloc(sizeof(double) * d * N), *vb = malloc(sizeof(double) * d * N);
+  double *k1 = malloc(sizeof(double) * N), *k2 = malloc(sizeof(double) * N), *yh = malloc(sizeof(double) * N);
+  double *gt = malloc(sizeof(double) * d * N);
+  int st = (!va || !vb || !k1 || !k2 || !yh || !gt) ? ORC_ENOMEM : 0;
+  if (!st) memset(u, 0, sizeof(double) * d * N);
+  for (int j = 0; j < nt && !st; ++j) {
+    velocity_at(P, v, j * h, va);
+    velocity_at(P, v, (j + 1) * h, vb);
+    for (int i = 0; i < d && !st; ++i) {
+      double *ui = u + (long)i * N;
+      st = apply_L(P, va, ui, k1, gt);
+      if (st) break;
+      for (long x = 0; x < N; ++x) {
+        k1[x] += va[i * N + x];
+        yh[x] = ui[x] + h * k1[x];
+      }
+      st = apply_L(P, vb, yh, k2, gt);
+      if (st) break;
+      for (long x = 0; x < N; ++x) {
+        k2[x] += vb[i * N + x];
+        ui[x] = ui[x] + 0.5 * h * (k1[x] + k2[x]);
+      }
+    }
+  }
+  free(va); free(vb); free(k1); free(k2); free(yh); free(gt);
+  return st;
+}
+
+/* Gaussian presmoothing (Sec. 3.3.5 "Presmoothing"): out = G_sigma * in on the
+ * periodic domain, i.e. the Fourier multiplier exp(-sigma^2 |k|^2 / 2) with the
+ * full wavenumbers (Nyquist modes included). */
+int orc_smooth(const orc_prob *P, double sigma, const double *in, double *out) {
+  if (!prob_ok(P) || !(sigma >= 0.0)) return ORC_EINVAL;
+  long N = grid_N(P);
+  double *U = malloc(sizeof(double) * 2 * N);
+  if (!U) return ORC_ENOMEM;
+  int st = to_spectrum(P, in, U);
+  if (!st) {
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < N; ++x) {
+      int j[3];
+      unflatten(P, x, j);
+      double kk = 0.0;
+      for (int i = 0; i < P->d; ++i) {
+        double k = wavenumber(j[i], P->n[i]);
+        kk += k * k;
+      }
+      double g = exp(-0.5 * sigma * sigma * kk);
+      U[2 * x] *= g;
+      U[2 * x + 1] *= g;
+    }
+    st = from_spectrum(P, U, out);
+  }
+  free(U);
   return st;
 }
 
@@ -1225,6 +1335,197 @@ int orc_solve(const orc_prob *P, const orc_opts *O, const double *mT, const doub
   if (!st && maxed) st = ORC_EMAXIT;
   R->status = st;
   free(g); free(s); free(r); free(z); free(p); free(Hp); free(vtrial);
+  return st;
+}
+
+/* Lanczos tridiagonalisation (Sec. 3.3.5 "Regularization": the condition
+ * number of the Hessian estimated with the Lanczos algorithm, Golub & Van
+ * Loan Sec. 9.1): k steps of the three-term recurrence on the Hessian at v
+ * (Gauss-Newton, or full Newton with mR when newton = 1), from q0. With
+ * precond = 1 the recurrence runs on P^{-1} H in the P inner product
+ * (P^{-1} = orc_precond). Plain coefficient-vector inner products, no
+ * reorthogonalisation. alpha[j] = q_j^T H q_j, beta[j] couples q_j and
+ * q_{j+1}; *steps = steps completed (fewer than k after a breakdown
+ * beta = 0). The eigenvalues of the tridiagonal matrix are the Ritz values. */
+int orc_lanczos(const orc_prob *P, const double *v, const double *mT, const double *mR, int newton,
+                const double *q0, int k, int precond, double *alpha, double *beta, int *steps) {
+  if (!prob_ok(P) || k < 1 || (newton && (P->dto || !mR))) return ORC_EINVAL;
+  long n = (long)P->n_c * P->d * grid_N(P);
+  double *q = malloc(sizeof(double) * n), *u = malloc(sizeof(double) * n);
+  double *up = calloc(n, sizeof(double));
+  double *w = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+  int st = (!q || !u || !up || !w || !z) ? ORC_ENOMEM : 0;
+  *steps = 0;
+  /* q_0 (primal) and u_0 = P q_0 (dual); without precond u = q */
+  if (!st) {
+    memcpy(u, q0, sizeof(double) * n);
+    if (precond) st = orc_precond(P, u, q);
+    else memcpy(q, u, sizeof(double) * n);
+  }
+  if (!st) {
+    double nrm = sqrt(dot(n, u, q));
+    if (!(nrm > 0.0)) st = ORC_EINVAL;
+    for (long i = 0; i < n && !st; ++i) {
+      q[i] /= nrm;
+      u[i] /= nrm;
+    }
+  }
+  double bprev = 0.0;
+  for (int j = 0; j < k && !st; ++j) {
+    st = newton ? orc_hessvec_newton(P, v, mT, mR, q, w) : orc_hessvec(P, v, mT, q, w);
+    if (st) break;
+    for (long i = 0; i < n; ++i) w[i] -= bprev * up[i];
+    double a = dot(n, q, w);
+    for (long i = 0; i < n; ++i) w[i] -= a * u[i];
+    if (precond) st = orc_precond(P, w, z);
+    else memcpy(z, w, sizeof(double) * n);
+    if (st) break;
+    double b2 = dot(n, w, z);
+    double b = b2 > 0.0 ? sqrt(b2) : 0.0;
+    alpha[j] = a;
+    beta[j] = b;
+    *steps = j + 1;
+    if (b == 0.0) break;
+    for (long i = 0; i < n; ++i) {
+      up[i] = u[i];
+      u[i] = w[i] / b;
+      q[i] = z[i] / b;
+    }
+    bprev = b;
+  }
+  free(q); free(u); free(up); free(w); free(z);
+  return st;
+}
+
+/* Parameter continuation in beta (Sec. 3.3.5 "Regularization"): solve at
+ * beta0, divide beta by 10 while min det F_1 >= eps_F (and the smallest grid
+ * angle >= eps_theta when eps_theta > 0), then bisect between the last
+ * accepted and the breaching beta until beta would change by less than
+ * beta_rtol times the first breaching beta. The reduction also ends at
+ * beta_min or when the relative L2 distance ||m_R - m_1|| / ||m_R - m_T||
+ * drops by less than the fraction dist_rtol. Each solve starts from the last
+ * accepted solution (from v before any); with cfl_target > 0 a solution above
+ * it raises n_t to ceil(n_t CFL / cfl_target) (at least n_t + 1) and solves
+ * again at the same beta. On return v is the accepted solution. */
+typedef struct {
+  double beta0, beta_min, eps_F, eps_theta, beta_rtol, dist_rtol, cfl_target;
+  int max_solves;
+} orc_cont_opts;
+
+typedef struct {
+  int found, stop, solves, n_t;
+  double beta, beta_breach, detF_min, angle_min, dist;
+  int n_trace;
+  double trace_beta[64], trace_detF[64], trace_angle[64], trace_dist[64];
+  int trace_ok[64];
+} orc_cont_report;
+
+int orc_continuation(const orc_prob *P0, const orc_opts *O, const orc_cont_opts *C, const double *mT,
+                     const double *mR, double *v, orc_cont_report *R) {
+  if (!prob_ok(P0)) return ORC_EINVAL;
+  orc_prob P = *P0;
+  long N = grid_N(&P);
+  long n = (long)P.n_c * P.d * N;
+  double *vstart = malloc(sizeof(double) * n), *vgood = malloc(sizeof(double) * n);
+  double *det = malloc(sizeof(double) * N), *ang = malloc(sizeof(double) * N);
+  int st = (!vstart || !vgood || !det || !ang) ? ORC_ENOMEM : 0;
+  memset(R, 0, sizeof(*R));
+  double base = 0.0;
+  for (long x = 0; x < N; ++x) base += (mR[x] - mT[x]) * (mR[x] - mT[x]);
+  if (!st) memcpy(vstart, v, sizeof(double) * n);
+  int have_good = 0, bisect = 0;
+  double beta_good = 0.0, beta_bad = 0.0, dist_prev = -1.0, beta = C->beta0;
+  while (!st) {
+    if (R->solves >= C->max_solves) {
+      R->stop = 4;
+      break;
+    }
+    P.beta = beta;
+    memcpy(v, have_good ? vgood : vstart, sizeof(double) * n);
+    orc_report sr;
+    int ss = orc_solve(&P, O, mT, mR, v, &sr);
+    R->solves += 1;
+    /* a solve ended by the iteration cap or a failed line search keeps its last iterate */
+    if (ss != 0 && ss != ORC_EMAXIT && ss != ORC_ELINESEARCH) {
+      st = ss;
+      break;
+    }
+    if (C->cfl_target > 0.0) {
+      double cf = orc_cfl(&P, v);
+      if (cf > C->cfl_target) {
+        int want = (int)ceil(P.n_t * cf / C->cfl_target);
+        P.n_t = want > P.n_t + 1 ? want : P.n_t + 1;
+        continue;
+      }
+    }
+    double out3[3];
+    st = orc_objective(&P, v, mT, mR, out3);
+    if (!st) st = orc_detF(&P, v, det);
+    if (!st) st = orc_grid_angle(&P, v, ang);
+    if (st) break;
+    double dmin = det[0], amin = ang[0];
+    for (long x = 1; x < N; ++x) {
+      dmin = fmin(dmin, det[x]);
+      amin = fmin(amin, ang[x]);
+    }
+    double dist = base > 0.0 ? sqrt((2.0 * out3[1] / cell_volume(&P)) / base) : 0.0;
+    int ok = dmin >= C->eps_F && (C->eps_theta <= 0.0 || amin >= C->eps_theta);
+    if (R->n_trace < 64) {
+      int t = R->n_trace++;
+      R->trace_beta[t] = beta;
+      R->trace_detF[t] = dmin;
+      R->trace_angle[t] = amin;
+      R->trace_dist[t] = dist;
+      R->trace_ok[t] = ok;
+    }
+    if (ok) {
+      have_good = 1;
+      beta_good = beta;
+      memcpy(vgood, v, sizeof(double) * n);
+      R->detF_min = dmin;
+      R->angle_min = amin;
+      R->dist = dist;
+    }
+    if (!bisect) {
+      if (ok) {
+        if (dist_prev > 0.0 && dist_prev - dist < C->dist_rtol * dist_prev) {
+          R->stop = 2;
+          break;
+        }
+        dist_prev = dist;
+        if (beta / 10.0 < C->beta_min) {
+          R->stop = 1;
+          break;
+        }
+        beta /= 10.0;
+        continue;
+      }
+      R->beta_breach = beta;
+      if (!have_good) {
+        R->stop = 3;
+        break;
+      }
+      beta_bad = beta;
+      bisect = 1;
+    } else if (ok) {
+      beta_good = beta;
+    } else {
+      beta_bad = beta;
+    }
+    double next = 0.5 * (beta_good + beta_bad);
+    if (fabs(next - beta) < C->beta_rtol * R->beta_breach) {
+      R->stop = 0;
+      break;
+    }
+    beta = next;
+  }
+  if (!st) {
+    R->found = have_good;
+    if (have_good) memcpy(v, vgood, sizeof(double) * n);
+    R->beta = have_good ? beta_good : beta;
+    R->n_t = P.n_t;
+  }
+  free(vstart); free(vgood); free(det); free(ang);
   return st;
 }
 

@@ -78,6 +78,32 @@ class Report(ctypes.Structure):
     ]
 
 
+class ContOpts(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in
+                ("beta0", "beta_min", "eps_F", "eps_theta", "beta_rtol", "dist_rtol", "cfl_target")] + [
+        ("max_solves", ctypes.c_int)]
+
+
+class ContReport(ctypes.Structure):
+    _fields_ = [
+        ("found", ctypes.c_int),
+        ("stop", ctypes.c_int),
+        ("solves", ctypes.c_int),
+        ("n_t", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("beta_breach", ctypes.c_double),
+        ("detF_min", ctypes.c_double),
+        ("angle_min", ctypes.c_double),
+        ("dist", ctypes.c_double),
+        ("n_trace", ctypes.c_int),
+        ("trace_beta", ctypes.c_double * 64),
+        ("trace_detF", ctypes.c_double * 64),
+        ("trace_angle", ctypes.c_double * 64),
+        ("trace_dist", ctypes.c_double * 64),
+        ("trace_ok", ctypes.c_int * 64),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``_build/liboracle.so`` (gcc, OpenMP, no FMA contraction)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
@@ -114,7 +140,15 @@ def lib():
                 "orc_hessvec": [P, dp, dp, dp, dp],
                 "orc_hessvec_newton": [P, dp, dp, dp, dp, dp],
                 "orc_detF": [P, dp, dp],
+                "orc_defgrad": [P, dp, dp],
+                "orc_grid_angle": [P, dp, dp],
+                "orc_displacement": [P, dp, dp],
+                "orc_smooth": [P, ctypes.c_double, dp, dp],
+                "orc_lanczos": [P, dp, dp, dp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp,
+                                ctypes.POINTER(ctypes.c_int)],
                 "orc_solve": [P, ctypes.POINTER(Opts), dp, dp, dp, ctypes.POINTER(Report)],
+                "orc_continuation": [P, ctypes.POINTER(Opts), ctypes.POINTER(ContOpts), dp, dp, dp,
+                                     ctypes.POINTER(ContReport)],
             }.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -257,6 +291,48 @@ class Problem:
         self._call("orc_detF", _ptr(v), _ptr(out))
         return out
 
+    def defgrad(self, v):
+        """F_1 of App. D Eq. def-grad, shape (d, d, *n)."""
+        v = _f64(v).reshape(self.coef_shape())
+        out = np.empty((self.d, self.d) + self.n)
+        self._call("orc_defgrad", _ptr(v), _ptr(out))
+        return out
+
+    def grid_angle(self, v):
+        """Per point, the smallest acute angle between deformed grid edges."""
+        v = _f64(v).reshape(self.coef_shape())
+        out = np.empty(self.n)
+        self._call("orc_grid_angle", _ptr(v), _ptr(out))
+        return out
+
+    def displacement(self, v):
+        """u_1 of App. D Eq. displacement, shape (d, *n); the map is y = x - u_1."""
+        v = _f64(v).reshape(self.coef_shape())
+        out = np.empty((self.d,) + self.n)
+        self._call("orc_displacement", _ptr(v), _ptr(out))
+        return out
+
+    def smooth(self, m, sigma):
+        """Gaussian presmoothing with standard deviation sigma."""
+        out = np.empty(self.n)
+        self._call("orc_smooth", float(sigma), _ptr(_f64(m)), _ptr(out))
+        return out
+
+    def lanczos(self, v, mT, q0, k, precond=False, mR=None, newton=False):
+        """k Lanczos steps on H (or P^{-1} H); returns (alpha, beta, ritz) with the
+        Ritz values (eigenvalues of the tridiagonal matrix) ascending."""
+        from scipy.linalg import eigvalsh_tridiagonal
+        v = _f64(v).reshape(self.coef_shape())
+        q0 = _f64(q0).reshape(self.coef_shape())
+        a, b = np.zeros(k), np.zeros(k)
+        steps = ctypes.c_int(0)
+        self._call("orc_lanczos", _ptr(v), _ptr(_f64(mT)), _ptr(None if mR is None else _f64(mR)), int(newton),
+                   _ptr(q0), int(k), int(bool(precond)), _ptr(a), _ptr(b), ctypes.byref(steps))
+        m = steps.value
+        a, b = a[:m], b[:m]
+        ritz = eigvalsh_tridiagonal(a, b[:m - 1]) if m > 1 else a.copy()
+        return a, b, ritz
+
     def cfl(self, v):
         v = _f64(v).reshape(self.coef_shape())
         return float(lib().orc_cfl(ctypes.byref(self._p), _ptr(v)))
@@ -277,6 +353,30 @@ class Problem:
         out = {f: getattr(rep, f) for f, _ in Report._fields_}
         out["status"] = st
         return v, out
+
+
+def continuation(problem, mT, mR, v0=None, beta0=1.0, beta_min=1e-6, eps_F=0.1, eps_theta=0.0, beta_rtol=0.05,
+                 dist_rtol=1e-2, cfl_target=0.0, max_solves=50, **solve_kw):
+    """Beta continuation (Sec. 3.3.5) on `problem` (its beta is the start of
+    nothing: beta0 is). Returns (v, report dict with the trace as lists)."""
+    v = np.zeros(problem.coef_shape()) if v0 is None else _f64(v0).reshape(problem.coef_shape()).copy()
+    so = dict(grad_rtol=1e-2, max_outer=50, armijo_c1=1e-4, backtrack=0.5, max_backtracks=20, pcg_maxit=0,
+              newton=False, picard=False, step_memory=True, stop_rule=0, tau_J=1e-3, cfl_max=0.0)
+    so.update(solve_kw)
+    opts = Opts(so["grad_rtol"], so["max_outer"], so["armijo_c1"], so["backtrack"], so["max_backtracks"],
+                so["pcg_maxit"], int(bool(so["newton"])), int(bool(so["picard"])), int(bool(so["step_memory"])),
+                int(so["stop_rule"]), float(so["tau_J"]), float(so["cfl_max"]))
+    co = ContOpts(beta0, beta_min, eps_F, eps_theta, beta_rtol, dist_rtol, cfl_target, max_solves)
+    rep = ContReport()
+    st = lib().orc_continuation(ctypes.byref(problem._p), ctypes.byref(opts), ctypes.byref(co), _ptr(_f64(mT)),
+                                _ptr(_f64(mR)), _ptr(v), ctypes.byref(rep))
+    if st != 0:
+        raise RuntimeError(f"orc_continuation failed with status {st}")
+    out = {}
+    for f, _ in ContReport._fields_:
+        val = getattr(rep, f)
+        out[f] = list(val)[:rep.n_trace] if f.startswith("trace_") else val
+    return v, out
 
 
 def fft(a, inverse=False):

@@ -687,3 +687,212 @@ def test_stopping_set_c4_at_a_stationary_start():
     c, P, _ = picard_problem()
     v, rep = P.solve(c["mT"], c["mT"], stop_rule=1)
     assert rep["status"] == 0 and rep["outer"] == 0 and rep["stop_flags"] & 8 and rep["g_inf"] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Presmoothing (Sec. 3.3.5 "Presmoothing"): the periodic Gaussian
+# ---------------------------------------------------------------------------
+
+def test_smoothing_single_modes_and_semigroup():
+    n = (32, 16)
+    P = O.Problem(n, 2)
+    X = synth.coords(n)
+    sigma = 2 * np.pi / 16
+    for k in [(1, 0), (3, 2), (16, 8), (5, 8)]:  # includes both Nyquist indices
+        m = np.cos(k[0] * X[0] + k[1] * X[1])
+        ref = np.exp(-0.5 * sigma ** 2 * (k[0] ** 2 + k[1] ** 2)) * m
+        assert np.abs(P.smooth(m, sigma) - ref).max() < 1e-13
+    m = rng(60).standard_normal(n)
+    a, b = 0.11, 0.23
+    assert np.abs(P.smooth(P.smooth(m, a), b) - P.smooth(m, np.hypot(a, b))).max() < 1e-13
+    assert abs(P.smooth(m, 0.4).mean() - m.mean()) < 1e-15
+    assert np.abs(P.smooth(m, 0.0) - m).max() < 1e-13
+
+
+def test_smoothing_a_point_mass_gives_the_periodised_gaussian():
+    n = (32, 32)
+    P = O.Problem(n, 2)
+    h = hd(n)
+    sigma = 0.6  # exp(-sigma^2 n^2 / 8) ~ 1e-20: the truncated spectrum is exact
+    e = np.zeros(n)
+    e[5, 9] = 1.0 / h  # unit mass
+    X = synth.coords(n)
+    x0 = (2 * np.pi * 5 / 32, 2 * np.pi * 9 / 32)
+    G = np.zeros(n)
+    for m1 in range(-3, 4):
+        for m2 in range(-3, 4):
+            r2 = (X[0] - x0[0] + 2 * np.pi * m1) ** 2 + (X[1] - x0[1] + 2 * np.pi * m2) ** 2
+            G += np.exp(-r2 / (2 * sigma ** 2)) / (2 * np.pi * sigma ** 2)
+    assert np.abs(P.smooth(e, sigma) - G).max() < 1e-12 * G.max()
+
+
+# ---------------------------------------------------------------------------
+# Deformation map (App. D Eq. displacement) and the deformation gradient /
+# grid-angle measure (App. D Eq. def-grad, Sec. 3.3.5 "Regularization")
+# ---------------------------------------------------------------------------
+
+def trig_eval(field, pts):
+    # exact evaluation of the trigonometric interpolant of `field` at arbitrary points
+    n = field.shape
+    F = np.fft.fftn(field) / field.size
+    ks = np.meshgrid(*[np.fft.fftfreq(k, 1.0 / k) for k in n], indexing="ij")
+    out = np.zeros(pts[0].size, dtype=complex)
+    flat = [p.ravel() for p in pts]
+    for idx in zip(*np.nonzero(np.abs(F) > 1e-15)):
+        phase = sum(ks[a][idx] * flat[a] for a in range(len(n)))
+        out += F[idx] * np.exp(1j * phase)
+    return out.real.reshape(pts[0].shape)
+
+
+def test_displacement_of_a_constant_velocity():
+    n = (16, 16)
+    P = O.Problem(n, 5)
+    v = np.zeros((1, 2) + n)
+    v[0, 0], v[0, 1] = 0.3, -0.7
+    u = P.displacement(v)
+    assert np.abs(u[0] - 0.3).max() < 1e-14 and np.abs(u[1] + 0.7).max() < 1e-14
+
+
+def test_displacement_map_pulls_back_the_template_at_second_order():
+    n = (32, 32)
+    r = rng(61)
+    mT = synth.random_spectral_field(n, r, 3.0)  # smooth enough that the spatial error stays below 1e-7
+    v = synth.velocity_field(n, r, 2, 0.4)[None]
+    X = synth.coords(n)
+    errs = []
+    for nt in (4, 8, 16, 32):
+        P = O.Problem(n, nt)
+        u = P.displacement(v)
+        m1 = P.state(v, mT)[-1]
+        pulled = trig_eval(mT, [X[0] - u[0], X[1] - u[1]])
+        errs.append(np.abs(pulled - m1).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+
+
+def test_deformation_gradient_and_grid_angle_of_a_shear():
+    # v = (s sin x2, 0): F_1 = I + grad v exactly (grad v is nilpotent and
+    # constant in time, and F does not vary along x1)
+    n = (16, 16)
+    s = 0.8
+    X = synth.coords(n)
+    v = np.zeros((1, 2) + n)
+    v[0, 0] = s * np.sin(X[1])
+    P = O.Problem(n, 7)
+    F = P.defgrad(v)
+    assert np.abs(F[0, 0] - 1).max() < 1e-13 and np.abs(F[1, 1] - 1).max() < 1e-13
+    assert np.abs(F[1, 0]).max() < 1e-13 and np.abs(F[0, 1] - s * np.cos(X[1])).max() < 1e-13
+    assert np.abs(P.detF(v) - 1).max() < 1e-13
+    c = np.abs(s * np.cos(X[1])) / np.sqrt(1 + (s * np.cos(X[1])) ** 2)
+    assert np.abs(P.grid_angle(v) - np.arccos(c)).max() < 1e-12
+    assert np.abs(P.grid_angle(np.zeros_like(v)) - np.pi / 2).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Lanczos (Sec. 3.3.5 "Regularization"): extreme Ritz values of H and P^{-1} H
+# ---------------------------------------------------------------------------
+
+def dense_hessian(P, v, mT):
+    n = int(np.prod(P.coef_shape()))
+    H = np.empty((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        H[:, i] = P.hessvec(v, mT, e).ravel()
+    return H
+
+
+def test_lanczos_extremes_match_dense_eigenvalues():
+    n = (8, 8)
+    r = rng(62)
+    P = O.Problem(n, 3, 1, 1e-2, 1, False, dto=True)  # symmetric discrete-adjoint Hessian
+    mT = synth.random_spectral_field(n, r, 3.0)
+    v = synth.velocity_field(n, r, 2, 0.3)[None]
+    H = dense_hessian(P, v, mT)
+    assert np.abs(H - H.T).max() < 1e-12 * np.abs(H).max()
+    ev = np.linalg.eigvalsh(H)
+    q0 = r.standard_normal(P.coef_shape())
+    a, b, ritz = P.lanczos(v, mT, q0, 60)
+    assert abs(a[0] - (q0.ravel() @ H @ q0.ravel()) / (q0.ravel() @ q0.ravel())) < 1e-12 * ev[-1]
+    assert abs(ritz[-1] - ev[-1]) < 1e-10 * ev[-1] and abs(ritz[0] - ev[0]) < 1e-8 * ev[-1]
+    # preconditioned: the eigenvalues of P^{-1} H
+    m = H.shape[0]
+    Pi = np.empty((m, m))
+    for i in range(m):
+        e = np.zeros(m)
+        e[i] = 1.0
+        Pi[:, i] = P.precond(e.reshape(P.coef_shape())).ravel()
+    evp = np.sort(np.linalg.eigvals(Pi @ H).real)
+    _, _, rp = P.lanczos(v, mT, q0, 60, precond=True)
+    assert abs(rp[-1] - evp[-1]) < 1e-10 * evp[-1] and abs(rp[0] - evp[0]) < 1e-8 * evp[-1]
+
+
+def test_lanczos_reproduces_the_printed_beta_1e6_maxima():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "eigen_beta1e6_64.txt")) if not ln.startswith("#")]
+    c = synth.blobs_2d(64, n_t=8)
+    for reg_name, stokes, value, digits in rows:
+        P = O.Problem((64, 64), 8, beta=1e6, reg=1 if reg_name == "H1" else 2, stokes=bool(int(stokes)))
+        q0 = rng(63).standard_normal(P.coef_shape())
+        _, _, ritz = P.lanczos(c["v_true"], c["mT"], q0, 40)
+        assert float(f"{ritz[-1]:.{int(digits) - 1}e}") == float(value), (reg_name, ritz[-1])
+
+
+# ---------------------------------------------------------------------------
+# Beta continuation (Sec. 3.3.5 "Regularization"): the trace follows the rule
+# ---------------------------------------------------------------------------
+
+def continuation_problem():
+    c = synth.sinusoid_2d(32)
+    P = O.Problem(c["n"], 8, 1, 1.0, 1, False)
+    mR = O.Problem(c["n"], 16).state(2 * c["v_true"], c["mT"])[-1]
+    return c, P, mR
+
+
+def check_trace(r, eps_F, beta0=1.0, beta_rtol=0.05):
+    tb, ok = r["trace_beta"], r["trace_ok"]
+    assert tb[0] == beta0
+    k = 0
+    while k + 1 < len(tb) and ok[k]:  # reduction by one order of magnitude while accepted
+        assert np.isclose(tb[k + 1], tb[k] / 10, rtol=1e-15)
+        k += 1
+    good, bad = tb[k - 1], tb[k]  # then bisection between last accepted and breaching beta
+    assert r["beta_breach"] == bad
+    for j in range(k + 1, len(tb)):
+        assert np.isclose(tb[j], 0.5 * (good + bad), rtol=1e-15)
+        if ok[j]:
+            good = tb[j]
+        else:
+            bad = tb[j]
+    assert abs(0.5 * (good + bad) - tb[-1]) < beta_rtol * r["beta_breach"]  # stop: change below 5%
+    assert r["beta"] == good == min(b for b, o in zip(tb, ok) if o)
+    for d, o in zip(r["trace_detF"], ok):
+        assert (d >= eps_F) == bool(o)
+
+
+def test_continuation_follows_the_beta_rule():
+    c, P, mR = continuation_problem()
+    v, r = O.continuation(P, c["mT"], mR, eps_F=0.8, max_outer=20, pcg_maxit=100)
+    assert r["found"] == 1 and r["stop"] == 0
+    check_trace(r, 0.8)
+    # the returned v is the accepted solution: solving at its beta from it changes nothing
+    Pb = O.Problem(c["n"], 8, 1, r["beta"], 1, False)
+    assert abs(Pb.detF(v).min() - r["detF_min"]) < 1e-14
+
+
+def test_continuation_without_a_feasible_beta_and_the_grid_angle_bound():
+    c, P, mR = continuation_problem()
+    _, r = O.continuation(P, c["mT"], mR, eps_F=0.99, max_outer=20, pcg_maxit=100)
+    assert r["found"] == 0 and r["stop"] == 3 and r["solves"] == 1 and r["beta_breach"] == 1.0
+    # the grid-angle bound alone (eps_F = 0) decides acceptance
+    _, r = O.continuation(P, c["mT"], mR, eps_F=0.0, eps_theta=1.2, max_outer=20, pcg_maxit=100)
+    assert r["found"] == 1
+    for a, o in zip(r["trace_angle"], r["trace_ok"]):
+        assert (a >= 1.2) == bool(o)
+
+
+def test_continuation_raises_n_t_to_meet_the_cfl_target():
+    c, P, mR = continuation_problem()
+    v, r = O.continuation(P, c["mT"], mR, eps_F=0.8, cfl_target=0.05, max_outer=20, pcg_maxit=100)
+    assert r["n_t"] > 8
+    Pn = O.Problem(c["n"], r["n_t"], 1, r["beta"], 1, False)
+    assert Pn.cfl(v) <= 0.05
