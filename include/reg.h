@@ -192,6 +192,49 @@ REG_API reg_status reg_detF(reg_ctx* ctx, const double* v, int substeps, double*
 /* CFL number h_t * max_j max_i ||v_i(t_j)||_inf / h_x^i (Sec. 3.3.1). */
 REG_API reg_status reg_cfl(reg_ctx* ctx, const double* v, double* cfl_out);
 
+/* Grid-angle measure (Sec. 3.3.5 "Regularization": the acute angle of a
+ * deformed grid element). The edges e_c of a cell map to the columns F_1 e_c
+ * of F_1 (App. D Eq. def-grad, substeps*n_t Heun steps); per point the
+ * result is the smallest min(theta, pi - theta) over column pairs, theta the
+ * angle between two columns, in radians (pi/2 for F = I). stats: host
+ * double[4] {min, max, mean, std}; angle (may be NULL): N doubles. */
+REG_API reg_status reg_grid_angle(reg_ctx* ctx, const double* v, int substeps, double* stats, double* angle);
+
+/* Deformation map (App. D Eq. displacement): du/dt + (grad u) v = v, u_0 = 0,
+ * Heun steps on the time nodes as in the state equation. u: d*N doubles, the
+ * displacement u_1 (component-major); the map is y = x - u_1. */
+REG_API reg_status reg_displacement(reg_ctx* ctx, const double* v, double* u);
+
+/* Gaussian presmoothing of an image (Sec. 3.3.5 "Presmoothing"): out = the
+ * periodic Gaussian of standard deviation sigma >= 0 (domain units, the paper
+ * uses 2*pi/min(n)) applied to in, i.e. the Fourier multiplier
+ * exp(-sigma^2 |k|^2 / 2) with the full wavenumbers. in, out: N doubles (may
+ * alias). Typically applied to m_T and m_R before reg_set_images. */
+REG_API reg_status reg_smooth(reg_ctx* ctx, double sigma, const double* in, double* out);
+
+/* Lanczos estimate of the Hessian spectrum (Sec. 3.3.5 "Regularization":
+ * the condition number estimated with the Lanczos algorithm): k steps of the
+ * three-term recurrence from q0 (n_c*d*N, any nonzero vector) on the Hessian
+ * at the linearisation point (as reg_hessvec applies it), or with precond = 1
+ * on P^{-1} H in the P inner product. Plain coefficient-vector inner
+ * products, no reorthogonalisation (the extreme Ritz values converge first).
+ * alpha, beta: host double[k], the tridiagonal matrix (beta[j] couples steps
+ * j and j+1); *steps: steps completed (< k after an exact breakdown);
+ * ritz (host double[k], may be NULL): its eigenvalues ascending. Requires a
+ * linearisation point (REG_ENOTREADY). */
+REG_API reg_status reg_lanczos(reg_ctx* ctx, const double* q0, int k, int precond, double* alpha, double* beta,
+                               int* steps, double* ritz);
+
+/* Change the regularisation weight beta of the context (beta continuation,
+ * Sec. 3.3.5). The linearisation point stays valid: only the regularisation
+ * and preconditioner terms depend on beta. */
+REG_API reg_status reg_set_beta(reg_ctx* ctx, double beta);
+
+/* Change the number of time steps n_t (a multiple of ckpt_every), e.g. to
+ * keep the CFL number bounded (Sec. 3.3.5 "PDE Solver"). Invalidates the
+ * linearisation point. */
+REG_API reg_status reg_set_time_steps(reg_ctx* ctx, int n_t);
+
 typedef struct {
   double grad_rtol;     /* stop at ||g_k||_inf <= grad_rtol ||g_0||_inf (Sec. 3.3.5) */
   int max_outer;        /* outer iteration cap n_opt */
@@ -281,6 +324,52 @@ typedef struct {
  * reg_last_error(NULL). Each problem's arrays must stay valid until return. */
 REG_API reg_status reg_solve_batched(const reg_problem* problems, int count, int precision, const reg_solve_opts* opts,
                                      reg_solve_report* reports, int workers);
+
+/* Parameter continuation in beta (Sec. 3.3.5 "Regularization"). */
+typedef struct {
+  double beta0;       /* first beta, large enough to underfit (1) */
+  double beta_min;    /* lower bound on beta (1e-6) */
+  double eps_F;       /* lower bound on min det F_1, in (0, 1) (0.1); 0 disables */
+  double eps_theta;   /* lower bound on the smallest grid angle in radians (0 = off; pi/16 in Sec. 5) */
+  double beta_rtol;   /* the bisection ends when beta changes by less than beta_rtol times
+                         the first beta that breached a bound (0.05) */
+  double dist_rtol;   /* the reduction ends when ||m_R - m_1||_2 drops by less than this fraction (1e-2) */
+  double cfl_target;  /* > 0: after a solve whose CFL number exceeds it, raise n_t in proportion
+                         (a multiple of ckpt_every) and solve again at the same beta (0 = off) */
+  int detF_substeps;  /* substeps of the det F_1 / grid-angle evaluation (1) */
+  int max_solves;     /* cap on registration solves (50) */
+} reg_cont_opts;
+
+#define REG_CONT_TRACE 64
+typedef struct {
+  int found;           /* 1 if some beta met the bounds: beta and v are that solution */
+  int stop;            /* 0 bisection converged, 1 beta_min reached, 2 distance stalled,
+                          3 no feasible beta (beta0 breached), 4 max_solves */
+  double beta;         /* the smallest accepted beta (the last one tried if none) */
+  double beta_breach;  /* first beta that breached a bound (0: none) */
+  int solves;          /* registration solves */
+  int n_t;             /* time steps at the end */
+  long outer, pcg_iters, matvecs;
+  double detF_min, angle_min, dist_rel; /* at the result; dist_rel = ||m_R-m_1||^2/||m_R-m_T||^2 */
+  double seconds;
+  int n_trace;         /* per solve (first REG_CONT_TRACE): beta, min det F_1, min angle,
+                          relative L2 distance ||m_R-m_1||/||m_R-m_T||, accepted */
+  double trace_beta[REG_CONT_TRACE], trace_detF[REG_CONT_TRACE], trace_angle[REG_CONT_TRACE];
+  double trace_dist[REG_CONT_TRACE];
+  int trace_ok[REG_CONT_TRACE];
+} reg_cont_report;
+
+REG_API void reg_cont_opts_default(reg_cont_opts* opts);
+
+/* Beta continuation: solve at beta0, divide beta by 10 while the solution
+ * keeps min det F_1 >= eps_F (and the smallest grid angle >= eps_theta),
+ * then bisect between the last accepted and the first breaching beta. Each
+ * solve (reg_solve with solve_opts) starts from the last accepted solution
+ * (from v_inout before any). On return v_inout holds the accepted solution
+ * and the context's beta is its beta. report: host. REG_OK also when no beta
+ * was feasible (report->found = 0). */
+REG_API reg_status reg_continuation(reg_ctx* ctx, double* v_inout, const reg_solve_opts* solve_opts,
+                                    const reg_cont_opts* cont_opts, reg_cont_report* report);
 
 /* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the kernels).

@@ -171,5 +171,7 @@ void spec_tail(const Grid& g, cudaStream_t s, const double2* V, const double2* F
 // out_l = sum_l' Ci[l][l'] s(k) R_l' with s = 1/(beta a(k)), s = 1 at k = 0.
 void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out, int nc, double beta,
                   const double* Ci_dev, int reg);
+// Gaussian filter exp(-sigma^2 |k|^2 / 2) of one packed FP64 field (out may not alias U)
+void spec_gauss(const Grid& g, cudaStream_t s, double2* U, double2* out, double sigma);
 
 }  // namespace reg

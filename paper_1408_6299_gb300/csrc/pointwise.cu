@@ -142,6 +142,28 @@ __global__ void k_identity_tensor(double* __restrict__ F, int d, long N) {
     for (int c = 0; c < d; ++c) F[(a * d + c) * N + x] = (a == c) ? 1.0 : 0.0;
 }
 
+// per point, the smallest acute angle between two columns F e_c (deformed grid edges)
+__global__ void k_grid_angle(const double* __restrict__ F, double* __restrict__ ang, int d, long N) {
+  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  const double half_pi = 1.5707963267948966;
+  double best = half_pi;
+  for (int c1 = 0; c1 < d; ++c1)
+    for (int c2 = c1 + 1; c2 < d; ++c2) {
+      double p = 0.0, n1 = 0.0, n2 = 0.0;
+      for (int a = 0; a < d; ++a) {
+        double f1 = F[(a * d + c1) * N + x], f2 = F[(a * d + c2) * N + x];
+        p += f1 * f2;
+        n1 += f1 * f1;
+        n2 += f2 * f2;
+      }
+      double cs = fmin(1.0, fmax(-1.0, p / sqrt(n1 * n2)));
+      double th = acos(cs);
+      best = fmin(best, th < half_pi ? th : 2.0 * half_pi - th);
+    }
+  ang[x] = best;
+}
+
 __global__ void k_det(const double* __restrict__ F, double* __restrict__ det, int d, long N) {
   long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
@@ -348,6 +370,10 @@ void identity_tensor(double* F, int d, long N, cudaStream_t s) {
 }
 void det_tensor(const double* F, double* det, int d, long N, cudaStream_t s) {
   k_det<<<nblk(N), 256, 0, s>>>(F, det, d, N);
+  REG_LAUNCH();
+}
+void grid_angle_tensor(const double* F, double* angle, int d, long N, cudaStream_t s) {
+  k_grid_angle<<<nblk(N), 256, 0, s>>>(F, angle, d, N);
   REG_LAUNCH();
 }
 void axpby(double a, const double* x, double b, double* y, long n, cudaStream_t s) {

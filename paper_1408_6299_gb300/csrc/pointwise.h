@@ -47,6 +47,8 @@ void detF_rhs(const double* G, const double* vt, const double* gv, const double*
               cudaStream_t s);
 void identity_tensor(double* F, int d, long N, cudaStream_t s);
 void det_tensor(const double* F, double* det, int d, long N, cudaStream_t s);
+// smallest acute angle between deformed grid edges (columns of F) per point
+void grid_angle_tensor(const double* F, double* angle, int d, long N, cudaStream_t s);
 
 // out = a x + b y in precision T (y may be null: out = a x; out may alias x or y)
 template <typename T>

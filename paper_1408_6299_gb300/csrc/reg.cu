@@ -138,7 +138,10 @@ struct reg_ctx {
   DBuf<double> tmpA, tmpB;  // coefficient-vector temporaries
   DBuf<double> stage_in[3], stage_out;  // staging of host arrays
   // det F scratch
-  DBuf<double> F, Fh, K1, K2, gvl, gvt, det;
+  DBuf<double> F, Fh, K1, K2, gvl, gvt, det, ang;
+  DBuf<double> disp_src;                          // sources -v_i(t) of the deformation map
+  DBuf<double> lz_q, lz_u, lz_up, lz_w, lz_z;     // Lanczos vectors
+  DBuf<double> ct_start, ct_good;                 // continuation iterates
   // solve vectors
   DBuf<double> sv_g, sv_s, sv_r, sv_z, sv_p, sv_Hp, sv_vt;
   KernelProfiler prof;  // CUDA-event bracketing of launches by kind (off unless enabled)
@@ -726,6 +729,11 @@ size_t graph_signature(reg_ctx* c) {
                         c->w64.Gt.p,   c->w32.Gt.p};
   size_t h = 1469598103934665603ull;
   for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
+  // and the settings that change what the matvec computes
+  uint64_t bb;
+  std::memcpy(&bb, &c->beta, sizeof bb);
+  const uint64_t modes[] = {bb, (uint64_t)c->hess, (uint64_t)c->quad, (uint64_t)c->prec, (uint64_t)c->n_t};
+  for (uint64_t m : modes) h = (h ^ (size_t)m) * 1099511628211ull;
   return h;
 }
 
@@ -795,8 +803,8 @@ double cfl(reg_ctx* c, const double* v) {
   return c->h() * mx;
 }
 
-// det F_1 (App. D Eq. def-grad) with substeps * n_t Heun steps
-void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_out) {
+// F_1 (App. D Eq. def-grad) with substeps * n_t Heun steps; returns c->F
+double* defgrad(reg_ctx* c, const double* v, int substeps) {
   const long N = c->N(), dN = c->dN();
   const int d = c->d, dd = d * d, nc = c->n_c;
   const long ddN = (long)dd * N;
@@ -839,9 +847,155 @@ void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_o
       }
     }
   }
+  return F;
+}
+
+// det F_1 statistics {min, max, mean, std} (and the field, if det_out)
+void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_out) {
+  const long N = c->N();
+  double* F = defgrad(c, v, substeps);
   double* det = det_out ? det_out : c->det.get(N);
-  det_tensor(F, det, d, N, c->s);
+  det_tensor(F, det, c->d, N, c->s);
   stats(det, N, red(c), c->s, st);
+}
+
+// det F_1 and grid-angle statistics from one F_1 (either field output may be null)
+void deform_measures(reg_ctx* c, const double* v, int substeps, double det_st[4], double ang_st[4], double* det_out,
+                     double* ang_out) {
+  const long N = c->N();
+  double* F = defgrad(c, v, substeps);
+  double* det = det_out ? det_out : c->det.get(N);
+  det_tensor(F, det, c->d, N, c->s);
+  stats(det, N, red(c), c->s, det_st);
+  double* ang = ang_out ? ang_out : c->ang.get(N);
+  grid_angle_tensor(F, ang, c->d, N, c->s);
+  stats(ang, N, red(c), c->s, ang_st);
+}
+
+// Gaussian presmoothing of one FP64 field (Sec. 3.3.5 "Presmoothing")
+void smooth(reg_ctx* c, double sigma, const double* in, double* out) {
+  const long Nc = c->g.Nc;
+  double2* S = c->SV.get((size_t)c->n_c * c->d * Nc);
+  double2* T = c->SF.get((size_t)c->n_c * c->d * Nc);
+  c->sp64->fwd(in, S);
+  spec_gauss(c->g, c->s, S, T, sigma);
+  c->sp64->inv(T, out);
+}
+
+// Deformation map (App. D Eq. displacement): du_i/dt = -v . grad u_i + v_i,
+// u_0 = 0, the same fused Heun stages as the state equation with the source
+// -v_i(t) (the stage subtracts its source). u: d fields.
+void displacement(reg_ctx* c, const double* v, double* u) {
+  Work<double>& w = c->w64;
+  const long N = c->N(), dN = c->dN();
+  double* yh = w.yh.get(N);
+  double* acc = w.acc.get(N);
+  double* va = w.va.get(dN);
+  double* vb = w.vb.get(dN);
+  double* s1 = c->disp_src.get(2 * N);
+  double* s2 = s1 + N;
+  REG_CUDA(cudaMemsetAsync(u, 0, dN * sizeof(double), c->s));
+  for (int j = 0; j < c->n_t; ++j) {
+    const double* vA = vel_node<double>(c, v, j, va);
+    const double* vB = vel_node<double>(c, v, j + 1, vb);
+    for (int i = 0; i < c->d; ++i) {
+      double* ui = u + (long)i * N;
+      lincomb_t<double>(-1.0, vA + (long)i * N, 0.0, nullptr, s1, N, c->s);
+      lincomb_t<double>(-1.0, vB + (long)i * N, 0.0, nullptr, s2, N, c->s);
+      adv<double>(c, ui, vA, nullptr, nullptr, ui, yh, acc, nullptr, 1, s1);
+      adv<double>(c, yh, vB, nullptr, nullptr, acc, ui, nullptr, nullptr, 2, s2);
+    }
+  }
+}
+
+// Eigenvalues of the symmetric tridiagonal matrix with diagonal a[0..m) and
+// off-diagonal b[0..m-1), ascending: bisection on Sturm counts (the number of
+// negative pivots of T - x I; Golub & Van Loan Sec. 8.4.1) inside the
+// Gershgorin interval.
+void tridiag_eigs(const double* a, const double* b, int m, double* out) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  const double scale = std::max(std::fabs(lo), std::fabs(hi));
+  const double tiny = DBL_MIN / DBL_EPSILON;
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double dd = a[0] - x;
+    if (dd < 0) ++cnt;
+    for (int i = 1; i < m; ++i) {
+      if (std::fabs(dd) < tiny) dd = dd < 0 ? -tiny : tiny;
+      dd = a[i] - x - b[i - 1] * b[i - 1] / dd;
+      if (dd < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int k = 0; k < m; ++k) {  // the k-th smallest eigenvalue lies where the count passes k
+    double l = lo, h = hi;
+    for (int it = 0; it < 200 && h - l > 2.0 * DBL_EPSILON * scale; ++it) {
+      double mid = 0.5 * (l + h);
+      if (count_below(mid) > k) h = mid;
+      else l = mid;
+    }
+    out[k] = 0.5 * (l + h);
+  }
+}
+
+// Lanczos three-term recurrence (Sec. 3.3.5 "Regularization"; Golub & Van
+// Loan Sec. 9.1) on the Hessian at the linearisation point, or on P^{-1} H in
+// the P inner product. Returns the number of steps completed.
+int lanczos(reg_ctx* c, const double* q0, int k, int use_precond, double* alpha, double* beta) {
+  const long n = c->ncdN();
+  double* q = c->lz_q.get(n);
+  double* u = c->lz_u.get(n);
+  double* up = c->lz_up.get(n);
+  double* w = c->lz_w.get(n);
+  double* z = c->lz_z.get(n);
+  double* rs = red(c);
+  REG_CUDA(cudaMemcpyAsync(u, q0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  if (use_precond) precond(c, u, q);
+  else REG_CUDA(cudaMemcpyAsync(q, u, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  double nrm2 = dot(u, q, n, rs, c->s);
+  if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) throw StatusError{REG_EINVAL, "the start vector has no positive norm"};
+  double nrm = std::sqrt(nrm2);
+  axpby(0.0, q, 1.0 / nrm, q, n, c->s);
+  axpby(0.0, u, 1.0 / nrm, u, n, c->s);
+  REG_CUDA(cudaMemsetAsync(up, 0, n * sizeof(double), c->s));
+  double bprev = 0.0;
+  int steps = 0;
+  for (int j = 0; j < k; ++j) {
+    hessvec(c, q, w);
+    axpby(-bprev, up, 1.0, w, n, c->s);
+    double a = dot(q, w, n, rs, c->s);
+    axpby(-a, u, 1.0, w, n, c->s);
+    if (use_precond) precond(c, w, z);
+    else REG_CUDA(cudaMemcpyAsync(z, w, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    double b2 = dot(w, z, n, rs, c->s);
+    check_finite(a, "Lanczos alpha");
+    check_finite(b2, "Lanczos beta");
+    double b = b2 > 0.0 ? std::sqrt(b2) : 0.0;
+    alpha[j] = a;
+    beta[j] = b;
+    steps = j + 1;
+    if (b == 0.0) break;
+    std::swap(up, u);  // u_{j-1} <- u_j, then u_{j+1} = w / b
+    lincomb(1.0 / b, w, 0.0, w, u, n, c->s);
+    lincomb(1.0 / b, z, 0.0, z, q, n, c->s);
+    bprev = b;
+  }
+  return steps;
+}
+
+// Time steps of the context (n_t) changed: node basis values, stored state invalid
+void set_time_steps(reg_ctx* c, int n_t) {
+  if (n_t < 1) throw StatusError{REG_EINVAL, "n_t must be >= 1"};
+  if (c->ckpt > 0 && n_t % c->ckpt != 0) throw StatusError{REG_EINVAL, "n_t must be a multiple of ckpt_every"};
+  c->n_t = n_t;
+  c->bnode.assign((size_t)(n_t + 1) * c->n_c, 0.0);
+  for (int j = 0; j <= n_t; ++j) cheb_values(c->n_c, (double)j / n_t, &c->bnode[(size_t)j * c->n_c]);
+  c->ready = false;
 }
 
 // ---------------------------------------------------------------------------
@@ -1007,6 +1161,115 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   R.status = status;
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// Parameter continuation in beta (Sec. 3.3.5 "Regularization"): reduce beta
+// by 10x from beta0 while the bounds on det F_1 (and the grid angle) hold,
+// then bisect between the last accepted and the breaching beta.
+// ---------------------------------------------------------------------------
+int continuation(reg_ctx* c, double* v, const reg_solve_opts& so, const reg_cont_opts& co, reg_cont_report& R) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!(co.beta0 > 0.0) || !(co.beta_min > 0.0) || !(co.beta_rtol > 0.0) || !(co.dist_rtol >= 0.0) ||
+      !(co.eps_F >= 0.0 && co.eps_F < 1.0) || !(co.eps_theta >= 0.0 && co.eps_theta < 0.5 * M_PI) ||
+      co.detF_substeps < 1 || co.max_solves < 1 || !(co.cfl_target >= 0.0))
+    throw StatusError{REG_EINVAL, "bad continuation options"};
+  const long n = c->ncdN();
+  double* vstart = c->ct_start.get(n);
+  double* vgood = c->ct_good.get(n);
+  REG_CUDA(cudaMemcpyAsync(vstart, v, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  std::memset(&R, 0, sizeof(R));
+  bool have_good = false, bisect = false;
+  double beta_good = 0.0, beta_bad = 0.0, dist_prev = -1.0;
+  double beta = co.beta0;
+  for (;;) {
+    if (R.solves >= co.max_solves) {
+      R.stop = 4;
+      break;
+    }
+    c->beta = beta;
+    REG_CUDA(cudaMemcpyAsync(v, have_good ? vgood : vstart, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    reg_solve_report sr;
+    int st = solve(c, v, so, sr);
+    R.solves += 1;
+    R.outer += sr.outer;
+    R.pcg_iters += sr.pcg_iters;
+    R.matvecs += sr.matvecs;
+    // a solve ended by the iteration cap or a failed line search keeps its last iterate
+    if (st != REG_OK && st != REG_EMAXIT && st != REG_ELINESEARCH)
+      throw StatusError{st, "a solve of the continuation failed"};
+    if (co.cfl_target > 0.0 && sr.cfl > co.cfl_target) {
+      // more time steps in proportion to the CFL excess, then the same beta again
+      const int K = c->ckpt > 0 ? c->ckpt : 1;
+      long want = (long)std::ceil(c->n_t * sr.cfl / co.cfl_target);
+      want = (want + K - 1) / K * K;
+      set_time_steps(c, (int)std::max<long>(want, c->n_t + K));
+      continue;
+    }
+    double dst[4], ast[4];
+    deform_measures(c, v, co.detF_substeps, dst, ast, nullptr, nullptr);
+    const double dist = std::sqrt(sr.dist_rel);
+    const bool ok = dst[0] >= co.eps_F && (co.eps_theta <= 0.0 || ast[0] >= co.eps_theta);
+    if (R.n_trace < REG_CONT_TRACE) {
+      int t = R.n_trace++;
+      R.trace_beta[t] = beta;
+      R.trace_detF[t] = dst[0];
+      R.trace_angle[t] = ast[0];
+      R.trace_dist[t] = dist;
+      R.trace_ok[t] = ok;
+    }
+    if (ok) {
+      have_good = true;
+      beta_good = beta;
+      REG_CUDA(cudaMemcpyAsync(vgood, v, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+      R.detF_min = dst[0];
+      R.angle_min = ast[0];
+      R.dist_rel = sr.dist_rel;
+    }
+    if (!bisect) {
+      if (ok) {
+        if (dist_prev > 0.0 && dist_prev - dist < co.dist_rtol * dist_prev) {
+          R.stop = 2;
+          break;
+        }
+        dist_prev = dist;
+        if (beta / 10.0 < co.beta_min) {
+          R.stop = 1;
+          break;
+        }
+        beta /= 10.0;
+        continue;
+      }
+      R.beta_breach = beta;
+      if (!have_good) {
+        R.stop = 3;
+        break;
+      }
+      beta_bad = beta;
+      bisect = true;
+    } else if (ok) {
+      beta_good = beta;
+    } else {
+      beta_bad = beta;
+    }
+    const double next = 0.5 * (beta_good + beta_bad);
+    if (std::fabs(next - beta) < co.beta_rtol * R.beta_breach) {
+      R.stop = 0;
+      break;
+    }
+    beta = next;
+  }
+  R.found = have_good;
+  if (have_good) {
+    REG_CUDA(cudaMemcpyAsync(v, vgood, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    c->beta = beta_good;
+  }
+  R.beta = c->beta;
+  R.n_t = c->n_t;
+  c->ready = false;
+  REG_CUDA(cudaStreamSynchronize(c->s));
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return REG_OK;
 }
 
 }  // namespace
@@ -1268,6 +1531,104 @@ reg_status reg_cfl(reg_ctx* ctx, const double* v, double* cfl_out) {
   if (!cfl_out) throw StatusError{REG_EINVAL, "cfl_out is null"};
   const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
   *cfl_out = cfl(c_, vd);
+  API_END
+}
+
+reg_status reg_grid_angle(reg_ctx* ctx, const double* v, int substeps, double* stats_out, double* angle_out) {
+  API_BEGIN(ctx)
+  if (substeps < 1) throw StatusError{REG_EINVAL, "substeps must be >= 1"};
+  if (!stats_out) throw StatusError{REG_EINVAL, "stats is null"};
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  double dst[4], ast[4];
+  if (angle_out) {
+    Output o(c_, angle_out, c_->N(), c_->stage_out);
+    deform_measures(c_, vd, substeps, dst, ast, nullptr, o.dev);
+    o.finish();
+  } else {
+    deform_measures(c_, vd, substeps, dst, ast, nullptr, nullptr);
+  }
+  for (int i = 0; i < 4; ++i) stats_out[i] = ast[i];
+  API_END
+}
+
+reg_status reg_displacement(reg_ctx* ctx, const double* v, double* u) {
+  API_BEGIN(ctx)
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  Output o(c_, u, c_->dN(), c_->stage_out);
+  if (o.dev == vd) throw StatusError{REG_EINVAL, "u may not alias v"};
+  displacement(c_, vd, o.dev);
+  o.finish();
+  API_END
+}
+
+reg_status reg_smooth(reg_ctx* ctx, double sigma, const double* in, double* out) {
+  API_BEGIN(ctx)
+  if (!(sigma >= 0.0) || !std::isfinite(sigma)) throw StatusError{REG_EINVAL, "sigma must be finite and >= 0"};
+  const double* id = input_ptr(c_, in, c_->N(), 0);
+  Output o(c_, out, c_->N(), c_->stage_out);
+  smooth(c_, sigma, id, o.dev);
+  o.finish();
+  API_END
+}
+
+reg_status reg_lanczos(reg_ctx* ctx, const double* q0, int k, int precond_flag, double* alpha, double* beta,
+                       int* steps, double* ritz) {
+  API_BEGIN(ctx)
+  if (k < 1) throw StatusError{REG_EINVAL, "k must be >= 1"};
+  if (!alpha || !beta || !steps) throw StatusError{REG_EINVAL, "null output argument"};
+  if (!c_->ready) throw StatusError{REG_ENOTREADY, "no linearisation point: call reg_gradient or reg_linearize first"};
+  const double* qd = input_ptr(c_, q0, c_->ncdN(), 0);
+  int m = lanczos(c_, qd, k, precond_flag ? 1 : 0, alpha, beta);
+  REG_CUDA(cudaStreamSynchronize(c_->s));
+  *steps = m;
+  if (ritz) tridiag_eigs(alpha, beta, m, ritz);
+  API_END
+}
+
+reg_status reg_set_beta(reg_ctx* ctx, double beta) {
+  API_BEGIN(ctx)
+  if (!(beta > 0.0) || !std::isfinite(beta)) throw StatusError{REG_EINVAL, "beta must be positive and finite"};
+  c_->beta = beta;
+  API_END
+}
+
+reg_status reg_set_time_steps(reg_ctx* ctx, int n_t) {
+  API_BEGIN(ctx)
+  set_time_steps(c_, n_t);
+  API_END
+}
+
+void reg_cont_opts_default(reg_cont_opts* o) {
+  if (!o) return;
+  o->beta0 = 1.0;
+  o->beta_min = 1e-6;
+  o->eps_F = 0.1;
+  o->eps_theta = 0.0;
+  o->beta_rtol = 0.05;
+  o->dist_rtol = 1e-2;
+  o->cfl_target = 0.0;
+  o->detF_substeps = 1;
+  o->max_solves = 50;
+}
+
+reg_status reg_continuation(reg_ctx* ctx, double* v_inout, const reg_solve_opts* solve_opts,
+                            const reg_cont_opts* cont_opts, reg_cont_report* report) {
+  API_BEGIN(ctx)
+  if (!c_->have_images) throw StatusError{REG_EINVAL, "reg_set_images has not been called"};
+  reg_solve_opts so;
+  reg_solve_opts_default(&so);
+  if (solve_opts) so = *solve_opts;
+  reg_cont_opts co;
+  reg_cont_opts_default(&co);
+  if (cont_opts) co = *cont_opts;
+  if (!v_inout) throw StatusError{REG_EINVAL, "v_inout is null"};
+  Output io(c_, v_inout, c_->ncdN(), c_->stage_out);
+  if (io.host)
+    REG_CUDA(cudaMemcpyAsync(io.dev, v_inout, c_->ncdN() * sizeof(double), cudaMemcpyHostToDevice, c_->s));
+  reg_cont_report R;
+  continuation(c_, io.dev, so, co, R);
+  io.finish();
+  if (report) *report = R;
   API_END
 }
 

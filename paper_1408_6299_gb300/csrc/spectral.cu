@@ -315,6 +315,27 @@ __global__ void k_spec_precond(const double2* __restrict__ R, double2* __restric
     }
 }
 
+// Gaussian filter exp(-sigma^2 |k|^2 / 2) on one packed field (full
+// wavenumbers, Nyquist kept; slot 0 of the last axis pairs k' with -k' as A does)
+__global__ void k_spec_gauss(double2* __restrict__ U, double2* __restrict__ out, GridArgs g, double s2) {
+  long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= g.Nc) return;
+  const int d = g.d;
+  ModeIdx m = decode(q, d, g.n, g.M);
+  double kk = lead_k2(m, g);
+  long kz = m.j[d - 1];
+  double2 v = U[q];
+  if (kz == 0) {
+    double g0 = exp(-0.5 * s2 * kk), gN = exp(-0.5 * s2 * (kk + 0.25 * (double)g.n[d - 1] * g.n[d - 1]));
+    double alpha = 0.5 * (g0 + gN), delta = 0.5 * (g0 - gN);
+    double2 vn = U[encode_neg(m, g)];
+    out[q] = make_double2(alpha * v.x + delta * vn.x, alpha * v.y - delta * vn.y);
+  } else {
+    double gk = exp(-0.5 * s2 * (kk + (double)kz * kz));
+    out[q] = make_double2(gk * v.x, gk * v.y);
+  }
+}
+
 GridArgs args(const Grid& g) {
   GridArgs a;
   a.d = g.d;
@@ -604,6 +625,11 @@ void spec_tail(const Grid& g, cudaStream_t s, const double2* V, const double2* F
 void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out, int nc, double beta,
                   const double* Ci_dev, int reg) {
   k_spec_precond<<<blocks_for(g.Nc), 256, 0, s>>>(R, out, args(g), nc, beta, Ci_dev, reg);
+  REG_LAUNCH();
+}
+
+void spec_gauss(const Grid& g, cudaStream_t s, double2* U, double2* out, double sigma) {
+  k_spec_gauss<<<blocks_for(g.Nc), 256, 0, s>>>(U, out, args(g), sigma * sigma);
   REG_LAUNCH();
 }
 

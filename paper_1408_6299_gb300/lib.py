@@ -104,6 +104,46 @@ class ProblemC(ctypes.Structure):
     ]
 
 
+class ContOpts(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in
+                ("beta0", "beta_min", "eps_F", "eps_theta", "beta_rtol", "dist_rtol", "cfl_target")] + [
+        ("detF_substeps", ctypes.c_int), ("max_solves", ctypes.c_int)]
+
+
+CONT_TRACE = 64
+
+
+class ContReport(ctypes.Structure):
+    _fields_ = [
+        ("found", ctypes.c_int),
+        ("stop", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("beta_breach", ctypes.c_double),
+        ("solves", ctypes.c_int),
+        ("n_t", ctypes.c_int),
+        ("outer", ctypes.c_long),
+        ("pcg_iters", ctypes.c_long),
+        ("matvecs", ctypes.c_long),
+        ("detF_min", ctypes.c_double),
+        ("angle_min", ctypes.c_double),
+        ("dist_rel", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("n_trace", ctypes.c_int),
+        ("trace_beta", ctypes.c_double * CONT_TRACE),
+        ("trace_detF", ctypes.c_double * CONT_TRACE),
+        ("trace_angle", ctypes.c_double * CONT_TRACE),
+        ("trace_dist", ctypes.c_double * CONT_TRACE),
+        ("trace_ok", ctypes.c_int * CONT_TRACE),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            val = getattr(self, name)
+            out[name] = list(val)[:self.n_trace] if name.startswith("trace_") else val
+        return out
+
+
 class RegError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -131,6 +171,13 @@ _SIGNATURES = {
     "reg_transport_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp],
     "reg_detF": [_vp, _vp, ctypes.c_int, _vp, _vp],
     "reg_cfl": [_vp, _vp, _vp],
+    "reg_grid_angle": [_vp, _vp, ctypes.c_int, _vp, _vp],
+    "reg_displacement": [_vp, _vp, _vp],
+    "reg_smooth": [_vp, ctypes.c_double, _vp, _vp],
+    "reg_lanczos": [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int), _vp],
+    "reg_set_beta": [_vp, ctypes.c_double],
+    "reg_set_time_steps": [_vp, ctypes.c_int],
+    "reg_continuation": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(ContOpts), ctypes.POINTER(ContReport)],
     "reg_solve": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
     "reg_precond_noalloc": [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                             _vp, _vp, _vp],
@@ -140,7 +187,8 @@ _SIGNATURES = {
     "reg_profile_end": [_vp, _vp, _vp, _vp],
 }
 
-EXPORTED = tuple(_SIGNATURES) + ("reg_last_error", "reg_solve_opts_default", "reg_launch_count")
+EXPORTED = tuple(_SIGNATURES) + ("reg_last_error", "reg_solve_opts_default", "reg_launch_count",
+                                  "reg_cont_opts_default")
 KIND_NAMES = ("rows_r2c", "rows_c2r", "cols", "mult", "stage", "force", "other")
 
 
@@ -209,6 +257,8 @@ def load(build_if_needed: bool = True):
             L.reg_last_error.restype = ctypes.c_char_p
             L.reg_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
             L.reg_solve_opts_default.restype = None
+            L.reg_cont_opts_default.argtypes = [ctypes.POINTER(ContOpts)]
+            L.reg_cont_opts_default.restype = None
             L.reg_launch_count.argtypes = []
             L.reg_launch_count.restype = ctypes.c_long
             _lib = L
@@ -346,6 +396,61 @@ class Registration:
         c = ctypes.c_double()
         self._check(self.L.reg_cfl(self.ctx, a, ctypes.byref(c)))
         return c.value
+
+    def grid_angle(self, v, substeps=1, out=None):
+        """Smallest acute angle between deformed grid edges: (min, max, mean, std)."""
+        a, ka = _addr(v)
+        b, kb = _addr(out)
+        st = (ctypes.c_double * 4)()
+        self._check(self.L.reg_grid_angle(self.ctx, a, int(substeps), st, b))
+        return tuple(st)
+
+    def displacement(self, v, u):
+        """u_1 of the deformation map into u (d fields)."""
+        a, ka = _addr(v)
+        b, kb = _addr(u)
+        self._check(self.L.reg_displacement(self.ctx, a, b))
+
+    def smooth(self, sigma, m, out):
+        """Gaussian presmoothing of m (N values) into out."""
+        a, ka = _addr(m)
+        b, kb = _addr(out)
+        self._check(self.L.reg_smooth(self.ctx, float(sigma), a, b))
+
+    def lanczos(self, q0, k, precond=False):
+        """(alpha, beta, ritz) of k Lanczos steps on H (or P^{-1} H) at the linearisation point."""
+        a, ka = _addr(q0)
+        al = (ctypes.c_double * k)()
+        be = (ctypes.c_double * k)()
+        rz = (ctypes.c_double * k)()
+        m = ctypes.c_int(0)
+        self._check(self.L.reg_lanczos(self.ctx, a, int(k), int(bool(precond)), al, be, ctypes.byref(m), rz))
+        m = m.value
+        return np.array(al[:m]), np.array(be[:m]), np.array(rz[:m])
+
+    def set_beta(self, beta):
+        self._check(self.L.reg_set_beta(self.ctx, float(beta)))
+
+    def set_time_steps(self, n_t):
+        self._check(self.L.reg_set_time_steps(self.ctx, int(n_t)))
+        self.n_t = int(n_t)
+
+    def continuation(self, v, solve_opts=None, **cont):
+        """Beta continuation in place on v; returns the report dict."""
+        so = SolveOpts.make(self.L, solve_opts or {})
+        co = ContOpts()
+        self.L.reg_cont_opts_default(ctypes.byref(co))
+        names = {f for f, _ in ContOpts._fields_}
+        for k, val in cont.items():
+            if k not in names:
+                raise TypeError(f"unknown continuation option {k!r}")
+            setattr(co, k, val)
+        a, ka = _addr(v)
+        rep = ContReport()
+        self._check(self.L.reg_continuation(self.ctx, a, ctypes.byref(so), ctypes.byref(co), ctypes.byref(rep)))
+        out = rep.as_dict()
+        self.n_t = out["n_t"]
+        return out
 
     def profile_begin(self, mask=(1 << 7) - 1):
         self._check(self.L.reg_profile_begin(self.ctx, int(mask)))

@@ -47,7 +47,8 @@ def test_create_without_device_fails_cleanly():
 def test_struct_layouts_match_the_header(tmp_path):
     # the ctypes mirrors of the header's structs: same size and field offsets
     import subprocess
-    structs = {"reg_solve_opts": lib.SolveOpts, "reg_solve_report": lib.SolveReport, "reg_problem": lib.ProblemC}
+    structs = {"reg_solve_opts": lib.SolveOpts, "reg_solve_report": lib.SolveReport, "reg_problem": lib.ProblemC,
+               "reg_cont_opts": lib.ContOpts, "reg_cont_report": lib.ContReport}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "reg.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
