@@ -154,42 +154,58 @@ struct RowsSpec {
 
 enum { EPI_ADV = 1, EPI_DIV = 2 };
 
-// Complex-to-real rows of NF fields, then the stage epilogue on the real
-// values (each thread handles a pair of neighbouring points). Fields whose
-// bit is set in zmask are multiplied by i k_last on load.
+// Hint: fetch a contiguous byte range into L2 (bulk prefetch; no completion to wait for).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The epilogue operands of one row block (elements [off, off + bytes) of each
+// operand field) are requested into L2 while the block loads and transforms
+// its spectra, so the epilogue finds them on chip. Threads 0..63 take one
+// operand each; only operands the epilogue will read are requested.
+template <typename T, int NF, int EPI>
+__device__ __forceinline__ void prefetch_epilogue(const AdvEpi<T>& adv, const DivEpi<T>& dv, long off,
+                                                  unsigned bytes) {
+  const int k = threadIdx.x;
+  if (k >= 64) return;
+  const T* p = nullptr;
+  if (EPI == EPI_ADV) {
+    if (adv.out1) {
+      if (k < NF) p = adv.a[k];
+      else if (k == NF) p = adv.y;
+      else if (k == NF + 1) p = adv.src;
+      else if (!adv.src && k < 2 * NF + 2) p = adv.gm[k - NF - 2];
+      else if (!adv.src && adv.gm[0] && k < 3 * NF + 2) p = adv.w[k - 2 * NF - 2];
+    }
+    if (adv.Sout && k >= 32 && k < 32 + NF) p = adv.sw[k - 32];
+  } else {
+    const long N = dv.N;
+    if (k == 0 && dv.stage >= 1) p = dv.y;
+    else if (k == 1) p = dv.src;
+    else if (dv.stage == 1 && dv.f_hi) {
+      const int nf = dv.nc * dv.d;
+      if (k == 2) p = dv.gmC ? dv.yC : nullptr;
+      else if (k >= 3 && k < 3 + dv.d) p = dv.gmA + (k - 3) * N;
+      else if (k >= 6 && k < 6 + dv.d) p = dv.gmB ? dv.gmB + (k - 6) * N : nullptr;
+      else if (k >= 9 && k < 9 + dv.d) p = dv.gmC ? dv.gmC + (k - 9) * N : nullptr;
+      else if (k >= 12 && k < 12 + nf) p = dv.f_hi + (long)(k - 12) * N;
+      else if (k >= 12 + nf && k < 12 + 2 * nf) p = dv.f_lo ? dv.f_lo + (long)(k - 12 - nf) * N : nullptr;
+    }
+  }
+  // the bulk prefetch wants a 16-byte aligned start (caller arrays may be offset views)
+  if (p && ((reinterpret_cast<unsigned long long>(p + off) | bytes) & 15) == 0) l2_prefetch(p + off, bytes);
+}
+
+// Inverse row transforms of one staged row block (NF fields x RB rows of
+// packed spectra in buf, padded rows of RS) and the stage epilogue of rows
+// row0..row0+RB-1. Called by all threads of the block after buf is complete.
 template <typename T, int L, int RB, int NF, int EPI>
-__global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int zmask, AdvEpi<T> adv,
-                                                          DivEpi<T> dv, long nrows, const cx<T>* __restrict__ tw,
-                                                          const cx<T>* __restrict__ twrc) {
+__device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
+                                          const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
+                                          const cx<T>* __restrict__ twrc) {
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
-  __shared__ C buf[NF * RB * RS];
-  const long row0 = (long)blockIdx.x * RB;
-  constexpr int PER = (NF * RB * M + kThreads - 1) / kThreads;
-  C v[PER];
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    int e = threadIdx.x + i * kThreads;
-    v[i] = mk<C>(0, 0);
-    if (e < NF * RB * M) {
-      int f = e / (RB * M), rem = e % (RB * M);
-      long row = row0 + rem / M;
-      if (row < nrows) v[i] = in.p[f][row * M + rem % M];
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    int e = threadIdx.x + i * kThreads;
-    if (e < NF * RB * M) {
-      int f = e / (RB * M), rem = e % (RB * M);
-      int j = rem % M;
-      C z = v[i];
-      if ((zmask >> f) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
-      buf[(f * RB + rem / M) * RS + pad16(j)] = z;
-    }
-  }
-  __syncthreads();
   constexpr int H = M / 2 + 1;
   for (int e = threadIdx.x; e < NF * RB * H; e += kThreads) {
     int seq = e / H, k = e % H;
@@ -335,6 +351,52 @@ __global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int
       }
     }
   }
+}
+
+
+// Complex-to-real rows of NF fields, then the stage epilogue on the real
+// values (each thread handles a pair of neighbouring points). Fields whose
+// bit is set in zmask are multiplied by i k_last on load.
+template <typename T, int L, int RB, int NF, int EPI>
+__global__ void __launch_bounds__(kThreads) k_rows_c2r_n(RowsSpec<T, NF> in, int zmask, AdvEpi<T> adv,
+                                                          DivEpi<T> dv, long nrows, const cx<T>* __restrict__ tw,
+                                                          const cx<T>* __restrict__ twrc) {
+  using C = cx<T>;
+  constexpr int M = L / 2;
+  constexpr int RS = padded_len(M);
+  __shared__ C buf[NF * RB * RS];
+  const long row0 = (long)blockIdx.x * RB;
+  constexpr int PER = (NF * RB * M + kThreads - 1) / kThreads;
+  C v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    v[i] = mk<C>(0, 0);
+    if (e < NF * RB * M) {
+      int f = e / (RB * M), rem = e % (RB * M);
+      long row = row0 + rem / M;
+      if (row < nrows) v[i] = in.p[f][row * M + rem % M];
+    }
+  }
+  // operand slices of at most 8 KB: larger blocks would prefetch more than the
+  // resident blocks of the whole GPU keep in L2 (measured: re-read traffic)
+  if constexpr (RB * L * sizeof(T) <= 8192) {
+    const long nr = nrows - row0 < RB ? nrows - row0 : RB;
+    prefetch_epilogue<T, NF, EPI>(adv, dv, row0 * L, (unsigned)(nr * L * sizeof(T)));
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int e = threadIdx.x + i * kThreads;
+    if (e < NF * RB * M) {
+      int f = e / (RB * M), rem = e % (RB * M);
+      int j = rem % M;
+      C z = v[i];
+      if ((zmask >> f) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
+      buf[(f * RB + rem / M) * RS + pad16(j)] = z;
+    }
+  }
+  __syncthreads();
+  c2r_block<T, L, RB, NF, EPI>(buf, row0, nrows, adv, dv, tw, twrc);
 }
 
 // Spectral derivative along a strided axis of length L on z-spectral rows:
