@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--no-solves", action="store_true")
     p.add_argument("--workload", default="matvec", choices=["matvec", "batch"])
     p.add_argument("--pairs", type=int, default=256)
-    p.add_argument("--batch-sample", type=int, default=32)
+    p.add_argument("--batch-sample", type=int, default=256)
+    p.add_argument("--batch-mode", default="lockstep", choices=["lockstep", "executor"])
     p.add_argument("--workers", type=int, default=8)
     return p.parse_args()
 
@@ -253,9 +254,10 @@ def batch_pairs(count):
     return pairs
 
 
-def solve_pairs(pairs, workers):
-    """reference images by the library's own transport, then one batched solve;
-    returns (seconds of the solve call, reports)"""
+def solve_pairs(pairs, workers, mode="lockstep"):
+    """reference images by the library's own transport, then one batched solve
+    (mode "lockstep": reg_solve_lockstep; "executor": reg_solve_batched with
+    `workers` threads); returns (seconds of the solve call, reports)"""
     import numpy as np
     import torch
 
@@ -275,21 +277,27 @@ def solve_pairs(pairs, workers):
         R.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    reps = lib.solve_batched(probs, precision=lib.REG_MIXED, workers=workers, grad_rtol=1e-2)
+    if mode == "lockstep":
+        reps = lib.solve_lockstep(probs, precision=lib.REG_MIXED, grad_rtol=1e-2)
+    else:
+        reps = lib.solve_batched(probs, precision=lib.REG_MIXED, workers=workers, grad_rtol=1e-2)
     torch.cuda.synchronize()
     return time.perf_counter() - t0, reps
 
 
 def batch_sample(count, workers):
     pairs = batch_pairs(count)
-    solve_pairs(pairs[:min(4, count)], workers)  # warm-up: tuning, tables
-    tb, reps = solve_pairs(pairs, workers)
-    ts, _ = solve_pairs(pairs, 1)
+    solve_pairs(pairs[:min(4, count)], workers, "executor")  # warm-up: tuning, tables
+    solve_pairs(pairs[:min(4, count)], workers, "lockstep")
+    tl, reps = solve_pairs(pairs, workers, "lockstep")
+    tb, repb = solve_pairs(pairs, workers, "executor")
+    ts, _ = solve_pairs(pairs, 1, "executor")
     ok = sum(1 for r in reps if r["status"] == 0 and r["g_inf"] <= 1e-2 * r["g0_inf"])
-    return {"pairs": count, "workers": workers, "batched_solves_per_s": count / tb,
-            "sequential_solves_per_s": count / ts, "speedup": ts / tb, "converged": ok,
-            "mean_outer": sum(r["outer"] for r in reps) / count,
-            "mean_matvecs": sum(r["matvecs"] for r in reps) / count}
+    return {"pairs": count, "lockstep_solves_per_s": count / tl, "executor_solves_per_s": count / tb,
+            "executor_workers": workers, "sequential_solves_per_s": count / ts, "speedup_vs_sequential": ts / tl,
+            "converged": ok, "mean_outer": sum(r["outer"] for r in reps) / count,
+            "mean_matvecs": sum(r["matvecs"] for r in reps) / count,
+            "same_outer_as_executor": sum(1 for a, b in zip(reps, repb) if a["outer"] == b["outer"])}
 
 
 def run_batch(args):
@@ -307,10 +315,10 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pairs = batch_pairs(args.pairs)
     mine = [pairs[i] for i in partition([p["n"][0] ** 2 * p["n_t"] for p in pairs], world)[rank]]
-    solve_pairs(mine[:4], args.workers)
+    solve_pairs(mine[:4], args.workers, args.batch_mode)
     if dist is not None:
         dist.barrier()
-    t, reps = solve_pairs(mine, args.workers)
+    t, reps = solve_pairs(mine, args.workers, args.batch_mode)
     if dist is not None:
         tt = torch.tensor([t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -320,7 +328,7 @@ def run_batch(args):
                           "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
                           "data": "synthetic", "dtype": "f32",
                           "config": {"workload": f"{args.pairs} 2D pairs 64^2/128^2/256^2 at 4:2:1, H1, n_c=1",
-                                     "workers_per_gpu": args.workers}}), flush=True)
+                                     "mode": args.batch_mode, "workers_per_gpu": args.workers}}), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -325,6 +325,25 @@ typedef struct {
 REG_API reg_status reg_solve_batched(const reg_problem* problems, int count, int precision, const reg_solve_opts* opts,
                                      reg_solve_report* reports, int workers);
 
+/* Lockstep batched solve of independent problems (Sec. 1.1 for each pair):
+ * problems of one shape, n_t, n_c, regulariser and scheme are stacked along
+ * an untransformed leading axis into one context (at most max_stack per
+ * stack; 0 = no limit), with one beta per problem. Every kernel of a matvec,
+ * gradient or objective evaluation covers the whole stack in one launch, and
+ * the stack's matvec is replayed as one captured CUDA graph. The outer loop of
+ * Alg. 1 (PCG or Picard, CFL halving, line search, stopping rule: opts) runs
+ * for all problems of a stack at once with per-problem Krylov and line-search
+ * scalars, so each problem takes the iterates it would take alone (up to the
+ * order of its inner-product sums); a problem that stops keeps its iterate
+ * while the others continue. Stacks run concurrently, one stream each.
+ * Checkpointing is off (every state gradient is stored). Arrays may be host
+ * or device memory; reports (may be NULL): one per problem, in the order of
+ * `problems`. Returns the status of the first failing stack; a problem that
+ * ends with REG_EMAXIT does not fail its stack. det F statistics are not
+ * computed (detF_substeps is ignored). */
+REG_API reg_status reg_solve_lockstep(const reg_problem* problems, int count, int precision,
+                                      const reg_solve_opts* opts, reg_solve_report* reports, int max_stack);
+
 /* Parameter continuation in beta (Sec. 3.3.5 "Regularization"). */
 typedef struct {
   double beta0;       /* first beta, large enough to underfit (1) */

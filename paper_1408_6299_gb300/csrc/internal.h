@@ -80,6 +80,9 @@ struct ProfScope {
 // N values; packed half spectra hold Nc = N/2 complex values laid out as
 // [n_0]..[n_{d-2}][M], M = n_{d-1}/2, where slot 0 of the last axis carries
 // uhat(k',0) + i*uhat(k',n_{d-1}/2) (DC and Nyquist columns of the last axis).
+// A grid of B independent problems of the same shape, stacked along an
+// untransformed leading axis (B = 1: one problem). N, Nc and rows count all
+// problems; every field is laid out [B][n_0]...[n_{d-1}].
 struct Grid {
   int d = 0;
   int n[3] = {1, 1, 1};
@@ -88,9 +91,11 @@ struct Grid {
   int L = 0;    // last-axis length
   int M = 0;    // L/2
   long rows = 0;  // N / L
+  int B = 1;      // stacked problems
+  long N1 = 0;    // real points of one problem
 };
 
-Grid make_grid(int d, const int64_t* n);
+Grid make_grid(int d, const int64_t* n, int batch = 1);
 
 // set the text that reg_last_error(NULL) returns on this thread
 void set_thread_error(const std::string& msg);
@@ -166,11 +171,12 @@ void div_stage(Spectral<T>& sp, const T* lam, const T* a, const fused::DivEpi<T>
 // DC/Nyquist pairing of the packed last-axis slot 0.
 // ---------------------------------------------------------------------------
 // out_l = beta sum_l' Cg[l][l'] a(k) V_l' + (stokes ? K F_l : F_l); F may be null.
+// betas (device, may be null): one beta per stacked problem, replacing beta.
 void spec_tail(const Grid& g, cudaStream_t s, const double2* V, const double2* F, double2* out, int nc,
-               double beta, const double* Cg_dev, int reg, int stokes);
+               double beta, const double* Cg_dev, int reg, int stokes, const double* betas = nullptr);
 // out_l = sum_l' Ci[l][l'] s(k) R_l' with s = 1/(beta a(k)), s = 1 at k = 0.
 void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out, int nc, double beta,
-                  const double* Ci_dev, int reg);
+                  const double* Ci_dev, int reg, const double* betas = nullptr);
 // Gaussian filter exp(-sigma^2 |k|^2 / 2) of one packed FP64 field (out may not alias U)
 void spec_gauss(const Grid& g, cudaStream_t s, double2* U, double2* out, double sigma);
 

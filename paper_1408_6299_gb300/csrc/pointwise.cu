@@ -387,6 +387,92 @@ void lincomb(double a, const double* x, double b, const double* y, double* out, 
 
 long reduce_scratch_doubles() { return 4L * kRedBlocks + 4; }
 
+// ---------------------------------------------------------------------------
+// Per-problem reductions and vector updates of B stacked problems: a vector
+// of K components is laid out [K][B][N1]; problem p owns the slices
+// [k][p][0..N1). Deterministic: fixed partial sums per (problem, block).
+// ---------------------------------------------------------------------------
+template <int OP>
+__global__ void k_seg_reduce(const double* __restrict__ a, const double* __restrict__ b, int K, int B, long N1,
+                             int nb, double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
+  const int p = blockIdx.y;
+  const long tot = (long)K * N1;
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * kRedThreads + threadIdx.x; i < tot; i += (long)nb * kRedThreads) {
+    const long idx = ((i / N1) * B + p) * N1 + i % N1;
+    const double u = a[idx];
+    if (OP == RED_DOT) acc += u * b[idx];
+    else if (OP == RED_SQDIFF) { double t = u - b[idx]; acc += t * t; }
+    else acc = fmax(acc, fabs(u));
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      sh[threadIdx.x] = OP == RED_MAXABS ? fmax(sh[threadIdx.x], sh[threadIdx.x + w]) : sh[threadIdx.x] + sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long)p * nb + blockIdx.x] = sh[0];
+}
+
+__global__ void k_seg_final(const double* __restrict__ part, int nb, int B, int is_max, double* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= B) return;
+  double acc = 0.0;
+  for (int j = 0; j < nb; ++j) acc = is_max ? fmax(acc, part[(long)p * nb + j]) : acc + part[(long)p * nb + j];
+  out[p] = acc;
+}
+
+// y = a_p x + c_p y per problem p (a zero coefficient drops its term, so a
+// masked problem's values never enter, whatever they hold)
+__global__ void k_axpby_seg(const double* __restrict__ a, const double* __restrict__ x,
+                            const double* __restrict__ c, const double* y, double* out, int B, long N1, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = (int)((i / N1) % B);
+  const double ap = a[p], cp = c[p];
+  out[i] = (ap != 0.0 ? ap * x[i] : 0.0) + (cp != 0.0 ? cp * y[i] : 0.0);
+}
+
+long seg_scratch_doubles(int B) { return (long)B * 32 + B; }
+
+void seg_reduce(int op, const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                double* out_host) {
+  const long tot = (long)K * N1;
+  int nb = (int)((tot + 8L * kRedThreads - 1) / (8L * kRedThreads));
+  nb = nb < 1 ? 1 : (nb > 32 ? 32 : nb);
+  dim3 grid((unsigned)nb, (unsigned)B);
+  switch (op) {
+    case RED_DOT: k_seg_reduce<RED_DOT><<<grid, kRedThreads, 0, s>>>(a, b, K, B, N1, nb, scratch); break;
+    case RED_SQDIFF: k_seg_reduce<RED_SQDIFF><<<grid, kRedThreads, 0, s>>>(a, b, K, B, N1, nb, scratch); break;
+    default: k_seg_reduce<RED_MAXABS><<<grid, kRedThreads, 0, s>>>(a, b, K, B, N1, nb, scratch); break;
+  }
+  REG_LAUNCH();
+  double* out = scratch + (long)B * 32;
+  k_seg_final<<<(B + 127) / 128, 128, 0, s>>>(scratch, nb, B, op == RED_MAXABS, out);
+  REG_LAUNCH();
+  REG_CUDA(cudaMemcpyAsync(out_host, out, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  REG_CUDA(cudaStreamSynchronize(s));
+}
+
+void seg_dot(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s, double* out) {
+  seg_reduce(RED_DOT, a, b, K, B, N1, scratch, s, out);
+}
+void seg_sqdiff(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                double* out) {
+  seg_reduce(RED_SQDIFF, a, b, K, B, N1, scratch, s, out);
+}
+void seg_maxabs(const double* a, int K, int B, long N1, double* scratch, cudaStream_t s, double* out) {
+  seg_reduce(RED_MAXABS, a, nullptr, K, B, N1, scratch, s, out);
+}
+void lincomb_seg(const double* a_dev, const double* x, const double* c_dev, const double* y, double* out, int K,
+                 int B, long N1, cudaStream_t s) {
+  const long n = (long)K * B * N1;
+  k_axpby_seg<<<nblk(n), 256, 0, s>>>(a_dev, x, c_dev, y, out, B, N1, n);
+  REG_LAUNCH();
+}
+
 // result (device, 4 doubles at scratch + 4*kRedBlocks): {sum, sumsq, min, max}
 static double* launch_reduce(int op, const double* a, const double* b, long n, double* scratch, cudaStream_t s,
                              double center = 0.0) {

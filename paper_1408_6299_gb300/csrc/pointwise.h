@@ -65,4 +65,16 @@ double sqdiff(const double* a, const double* b, long n, double* scratch, cudaStr
 double maxabs(const double* a, long n, double* scratch, cudaStream_t s);
 void stats(const double* a, long n, double* scratch, cudaStream_t s, double out[4]);
 
+// per-problem reductions of B stacked problems, vectors of K components laid
+// out [K][B][N1]; results (B values) to host memory; scratch holds
+// seg_scratch_doubles(B); synchronise the stream
+long seg_scratch_doubles(int B);
+void seg_dot(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s, double* out);
+void seg_sqdiff(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                double* out);
+void seg_maxabs(const double* a, int K, int B, long N1, double* scratch, cudaStream_t s, double* out);
+// out = a_p x + c_p y per problem p; a_dev, c_dev: B coefficients on the device (out may alias y)
+void lincomb_seg(const double* a_dev, const double* x, const double* c_dev, const double* y, double* out, int K,
+                 int B, long N1, cudaStream_t s);
+
 }  // namespace reg

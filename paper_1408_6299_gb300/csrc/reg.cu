@@ -13,6 +13,9 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <thread>
+#include <tuple>
 #include <memory>
 #include <new>
 #include <string>
@@ -112,6 +115,9 @@ struct Work {
 struct reg_ctx {
   int d = 0, n_t = 0, n_c = 0, rtype = 1, stokes = 0, prec = 0, ckpt = 0, quad = 0;
   int hess = 0;  // REG_HESS_GN or REG_HESS_NEWTON
+  // stacked problems (g.B > 1): one beta per problem, per-problem reductions
+  std::vector<double> betas;
+  DBuf<double> betas_dev, seg_scr, coefA, coefC, sv_v;
   double beta = 0;
   cudaStream_t s = nullptr;
   Grid g;
@@ -613,7 +619,8 @@ void tail(reg_ctx* c, const double* V, const double* F, double* out) {
     sp.fwd(V + q * N, SV + q * Nc);
     if (F) sp.fwd(F + q * N, SF + q * Nc);
   }
-  spec_tail(c->g, c->s, SV, F ? SF : nullptr, SF, c->n_c, c->beta, c->Cg_dev.p, c->rtype, c->stokes);
+  spec_tail(c->g, c->s, SV, F ? SF : nullptr, SF, c->n_c, c->beta, c->Cg_dev.p, c->rtype, c->stokes,
+            c->g.B > 1 ? c->betas_dev.p : nullptr);
   for (int q = 0; q < ncd; ++q) sp.inv(SF + q * Nc, out + q * N);
 }
 
@@ -624,7 +631,7 @@ void precond(reg_ctx* c, const double* r, double* z) {
   double2* SF = c->SF.get((size_t)ncd * Nc);
   Spectral<double>& sp = *c->sp64;
   for (int q = 0; q < ncd; ++q) sp.fwd(r + q * N, SV + q * Nc);
-  spec_precond(c->g, c->s, SV, SF, c->n_c, c->beta, c->Ci_dev.p, c->rtype);
+  spec_precond(c->g, c->s, SV, SF, c->n_c, c->beta, c->Ci_dev.p, c->rtype, c->g.B > 1 ? c->betas_dev.p : nullptr);
   for (int q = 0; q < ncd; ++q) sp.inv(SF + q * Nc, z + q * N);
 }
 
@@ -1272,6 +1279,332 @@ int continuation(reg_ctx* c, double* v, const reg_solve_opts& so, const reg_cont
   return REG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Stacked problems (g.B > 1): per-problem objective and gradient, and the
+// outer loop of Alg. 1 run for all problems in lockstep. Every kernel of a
+// matvec, gradient or objective evaluation covers all problems at once; the
+// Krylov and line-search scalars are per problem, so each problem follows
+// exactly the iteration it would follow alone. A problem that has stopped
+// keeps its iterate: its update coefficients are zero.
+// ---------------------------------------------------------------------------
+struct Seg {
+  reg_ctx* c;
+  int B, K;
+  long N1;
+  double* scr;
+  std::vector<double> tmp;
+  explicit Seg(reg_ctx* c_, int K_)
+      : c(c_), B(c_->g.B), K(K_), N1(c_->g.N1), scr(c_->seg_scr.get(seg_scratch_doubles(c_->g.B))), tmp(c_->g.B) {}
+  void dot(const double* a, const double* b, std::vector<double>& out) {
+    out.resize(B);
+    seg_dot(a, b, K, B, N1, scr, c->s, out.data());
+  }
+  void maxabs(const double* a, std::vector<double>& out) {
+    out.resize(B);
+    seg_maxabs(a, K, B, N1, scr, c->s, out.data());
+  }
+  // out = a_p x + b_p y (per-problem coefficients from the host)
+  void comb(const std::vector<double>& a, const double* x, const std::vector<double>& b, const double* y, double* out) {
+    double* da = c->coefA.get(B);
+    double* db = c->coefC.get(B);
+    REG_CUDA(cudaMemcpyAsync(da, a.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    REG_CUDA(cudaMemcpyAsync(db, b.data(), B * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    REG_CUDA(cudaStreamSynchronize(c->s));  // the host vectors may change after return
+    lincomb_seg(da, x, db, y, out, K, B, N1, c->s);
+  }
+};
+
+// per problem: distance 1/2 h_d ||m_R - m_1||^2 and regularisation of v
+void objective_seg(reg_ctx* c, const double* v, std::vector<double>& dist, std::vector<double>& regt) {
+  const long N = c->N();
+  Work<double>& w = c->w64;
+  REG_CUDA(cudaMemcpyAsync(w.m.get(N), c->mT.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  state_steps<double>(c, v, 0, c->n_t, nullptr, nullptr, 0, nullptr);
+  Seg one(c, 1), vec(c, c->n_c * c->d);
+  dist.resize(c->g.B);
+  seg_sqdiff(c->mR.p, w.m.p, 1, c->g.B, c->g.N1, one.scr, c->s, dist.data());
+  for (double& x : dist) x *= 0.5 * c->hd;
+  double* Rv = c->tmpB.get(c->ncdN());
+  tail(c, v, nullptr, Rv);
+  vec.dot(v, Rv, regt);
+  for (double& x : regt) x *= 0.5 * c->hd;
+}
+
+void gradient_seg(reg_ctx* c, const double* v, double* g, std::vector<double>& dist, std::vector<double>& regt) {
+  const long N = c->N();
+  set_point(c, v);
+  Work<double>& w = c->w64;
+  Seg one(c, 1), vec(c, c->n_c * c->d);
+  dist.resize(c->g.B);
+  seg_sqdiff(c->mR.p, w.m.p, 1, c->g.B, c->g.N1, one.scr, c->s, dist.data());
+  for (double& x : dist) x *= 0.5 * c->hd;
+  lincomb_t<double>(1.0, c->mR.p, -1.0, w.m.p, w.lam.get(N), N, c->s);
+  double* f = c->f.get(c->ncdN());
+  adjoint_solve<double>(c, c->vlin.p, f);
+  tail(c, c->vlin.p, f, g);
+  double* Rv = c->tmpB.get(c->ncdN());
+  tail(c, c->vlin.p, nullptr, Rv);
+  vec.dot(c->vlin.p, Rv, regt);
+  for (double& x : regt) x *= 0.5 * c->hd;
+  prepare_mixed(c);
+  c->ready = true;
+}
+
+// per-problem CFL number of coefficient vector v
+void cfl_seg(reg_ctx* c, const double* v, std::vector<double>& out) {
+  const int B = c->g.B;
+  const long N1 = c->g.N1, N = c->N(), dN = c->dN();
+  out.assign(B, 0.0);
+  Seg one(c, 1);
+  std::vector<double> m;
+  double* vt = c->tmpA.get(dN);
+  const int nodes = c->n_c == 1 ? 1 : c->n_t + 1;
+  for (int j = 0; j < nodes; ++j) {
+    const double* vj = v;
+    if (c->n_c > 1) {
+      vel_at<double, double>(v, c->n_c, c->basis_at_node(j), vt, dN, c->s);
+      vj = vt;
+    }
+    for (int i = 0; i < c->d; ++i) {
+      seg_maxabs(vj + (long)i * N, 1, B, N1, one.scr, c->s, (one.tmp.resize(B), one.tmp.data()));
+      const double hx = 2.0 * M_PI / c->g.n[i];
+      for (int p = 0; p < B; ++p) out[p] = std::max(out[p], c->h() * one.tmp[p] / hx);
+    }
+  }
+}
+
+void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report* R) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int B = c->g.B;
+  const long n = c->ncdN();
+  double* g = c->sv_g.get(n);
+  double* s = c->sv_s.get(n);
+  double* r = c->sv_r.get(n);
+  double* z = c->sv_z.get(n);
+  double* p = c->sv_p.get(n);
+  double* Hp = c->sv_Hp.get(n);
+  double* vt = c->sv_vt.get(n);
+  Seg sg(c, c->n_c * c->d);
+  const long maxit = o.pcg_maxit > 0 ? o.pcg_maxit : n / B;
+  std::vector<double> dist, regt, J(B), ginf, g2, g02, zero(B, 0.0), one(B, 1.0), tmp, tmp2;
+  std::vector<int> active(B, 1), k(B, 0);
+  std::vector<double> amem(B, 1.0);
+  for (int q = 0; q < B; ++q) std::memset(&R[q], 0, sizeof(reg_solve_report));
+  auto finite_or_fail = [&](int q, double x) {
+    if (active[q] && !std::isfinite(x)) {
+      active[q] = 0;
+      R[q].status = REG_ENONFINITE;
+    }
+  };
+  gradient_seg(c, v, g, dist, regt);
+  sg.maxabs(g, ginf);
+  sg.dot(g, g, tmp);
+  sg.maxabs(v, tmp2);
+  for (int q = 0; q < B; ++q) {
+    J[q] = dist[q] + regt[q];
+    R[q].n_pde = 2;
+    R[q].J0 = J[q];
+    R[q].g0_inf = ginf[q];
+    R[q].v_inf = tmp2[q];
+    R[q].alpha_mem = 1.0;
+    g02.push_back(std::sqrt(tmp[q]));
+    finite_or_fail(q, J[q] + tmp[q]);
+  }
+  for (;;) {
+    sg.maxabs(g, ginf);
+    sg.dot(g, g, tmp);
+    g2.assign(B, 0.0);
+    int live = 0;
+    for (int q = 0; q < B; ++q) {
+      g2[q] = std::sqrt(tmp[q]);
+      if (!active[q]) continue;
+      R[q].g_inf = ginf[q];
+      R[q].J = J[q];
+      bool maxed = false;
+      if (stop_test(o, R[q], k[q], ginf[q], maxed)) {
+        active[q] = 0;
+        R[q].status = maxed ? REG_EMAXIT : REG_OK;
+      } else {
+        ++live;
+      }
+    }
+    if (!live) break;
+    std::vector<double> act(B);
+    for (int q = 0; q < B; ++q) act[q] = active[q] ? 1.0 : 0.0;
+    if (o.method == REG_METHOD_PICARD) {
+      precond(c, g, s);
+      std::vector<double> sc(B);
+      for (int q = 0; q < B; ++q) sc[q] = active[q] ? (o.step_memory ? -amem[q] : -1.0) : 0.0;
+      sg.comb(zero, s, sc, s, s);
+    } else {
+      // PCG on H s = -g from s = 0, all active problems at once
+      std::vector<double> eta(B), rz, rzn, pHp, rn2, on(B);
+      for (int q = 0; q < B; ++q) {
+        eta[q] = std::min(0.5, std::sqrt(g2[q] / g02[q]));
+        on[q] = active[q];
+      }
+      REG_CUDA(cudaMemsetAsync(s, 0, n * sizeof(double), c->s));
+      REG_CUDA(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+      precond(c, r, z);
+      sg.comb(std::vector<double>(B, -1.0), z, zero, z, p);
+      sg.dot(r, z, rz);
+      for (long it = 0; it < maxit; ++it) {
+        sg.dot(r, r, rn2);
+        int running = 0;
+        for (int q = 0; q < B; ++q) {
+          if (!on[q]) continue;
+          finite_or_fail(q, rn2[q]);
+          if (!active[q] || std::sqrt(rn2[q]) <= eta[q] * g2[q]) on[q] = 0;
+          else ++running;
+        }
+        if (!running) break;
+        hessvec(c, p, Hp);
+        sg.dot(p, Hp, pHp);
+        std::vector<double> a(B, 0.0), cs(B, 1.0), copy_p(B, 0.0);
+        bool any_copy = false;
+        for (int q = 0; q < B; ++q) {
+          if (!on[q]) continue;
+          R[q].matvecs += 1;
+          R[q].n_pde += 2;
+          R[q].pcg_iters += 1;
+          finite_or_fail(q, pHp[q]);
+          if (!active[q]) {
+            on[q] = 0;
+          } else if (pHp[q] <= 0.0) {
+            if (it == 0) {
+              copy_p[q] = 1.0;
+              any_copy = true;
+            }
+            on[q] = 0;
+          } else {
+            a[q] = rz[q] / pHp[q];
+          }
+        }
+        if (any_copy) {  // negative curvature at the first step: the steepest-descent direction
+          std::vector<double> keep(B);
+          for (int q = 0; q < B; ++q) keep[q] = copy_p[q] != 0.0 ? 0.0 : 1.0;
+          sg.comb(copy_p, p, keep, s, s);
+        }
+        sg.comb(a, p, one, s, s);
+        sg.comb(a, Hp, one, r, r);
+        precond(c, r, z);
+        sg.dot(r, z, rzn);
+        std::vector<double> mz(B, 0.0), bt(B, 1.0);
+        for (int q = 0; q < B; ++q)
+          if (on[q]) {
+            mz[q] = -1.0;
+            bt[q] = rzn[q] / rz[q];
+            rz[q] = rzn[q];
+          }
+        sg.comb(mz, z, bt, p, p);
+      }
+    }
+    // keep each step inside the CFL bound by halving it (Sec. 3.3.5)
+    if (o.cfl_max > 0) {
+      std::vector<int> halvings(B, 0);
+      for (;;) {
+        sg.comb(one, v, one, s, vt);
+        std::vector<double> cf;
+        cfl_seg(c, vt, cf);
+        std::vector<double> h(B, 1.0);
+        bool any = false;
+        for (int q = 0; q < B; ++q) {
+          if (!active[q] || cf[q] <= o.cfl_max) continue;
+          if (++halvings[q] > 30) {
+            active[q] = 0;
+            R[q].status = REG_ECFL;
+            h[q] = 0.0;  // no step
+          } else {
+            h[q] = 0.5;
+            R[q].cfl_halvings += 1;
+          }
+          any = true;
+        }
+        if (!any) break;
+        sg.comb(zero, s, h, s, s);
+      }
+    }
+    // Armijo backtracking from alpha = 1, per problem
+    std::vector<double> slope, alpha(B, 0.0), Jt(B, 0.0);
+    sg.dot(g, s, slope);
+    for (double& x : slope) x *= c->hd;
+    std::vector<int> searching(B, 0);
+    int nsearch = 0;
+    for (int q = 0; q < B; ++q)
+      if (active[q]) {
+        alpha[q] = 1.0;
+        searching[q] = 1;
+        ++nsearch;
+      }
+    for (int t = 0; t < o.max_backtracks && nsearch; ++t) {
+      sg.comb(one, v, alpha, s, vt);
+      std::vector<double> d2, r2;
+      objective_seg(c, vt, d2, r2);
+      for (int q = 0; q < B; ++q) {
+        if (!searching[q]) continue;
+        R[q].ls_trials += 1;
+        R[q].n_pde += 1;
+        Jt[q] = d2[q] + r2[q];
+        if (std::isfinite(Jt[q]) && Jt[q] <= J[q] + o.armijo_c1 * alpha[q] * slope[q]) {
+          searching[q] = 0;
+          --nsearch;
+        } else {
+          alpha[q] *= o.backtrack;
+        }
+      }
+    }
+    for (int q = 0; q < B; ++q)
+      if (searching[q]) {  // no sufficient decrease: the problem keeps its iterate
+        active[q] = 0;
+        R[q].status = REG_ELINESEARCH;
+        alpha[q] = 0.0;
+      }
+    for (int q = 0; q < B; ++q) {
+      if (!active[q]) alpha[q] = 0.0;
+      if (active[q] && o.method == REG_METHOD_PICARD && o.step_memory)
+        amem[q] = (alpha[q] == 1.0) ? 2.0 * amem[q] : amem[q] * alpha[q];
+      R[q].alpha_mem = amem[q];
+    }
+    sg.comb(one, v, alpha, s, vt);
+    sg.comb(one, vt, std::vector<double>(B, -1.0), v, r);  // v_k - v_{k-1}
+    std::vector<double> dv, vin;
+    sg.maxabs(r, dv);
+    REG_CUDA(cudaMemcpyAsync(v, vt, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+    sg.maxabs(v, vin);
+    std::vector<int> stepped = active;
+    for (int q = 0; q < B; ++q)
+      if (stepped[q]) {
+        R[q].dv_inf = dv[q];
+        R[q].v_inf = vin[q];
+        R[q].J_prev = J[q];
+      }
+    gradient_seg(c, v, g, dist, regt);
+    for (int q = 0; q < B; ++q) {
+      if (!stepped[q]) continue;
+      J[q] = dist[q] + regt[q];
+      R[q].n_pde += 2;
+      k[q] += 1;
+      finite_or_fail(q, J[q]);
+    }
+  }
+  // final measures per problem
+  std::vector<double> base(B), cf;
+  {
+    Seg one1(c, 1);
+    seg_sqdiff(c->mT.p, c->mR.p, 1, B, c->g.N1, one1.scr, c->s, base.data());
+  }
+  cfl_seg(c, v, cf);
+  REG_CUDA(cudaStreamSynchronize(c->s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int q = 0; q < B; ++q) {
+    R[q].outer = k[q];
+    R[q].J = J[q];
+    R[q].dist_rel = base[q] > 0 ? (2.0 * dist[q] / c->hd) / base[q] : 0.0;
+    R[q].cfl = cf[q];
+    R[q].seconds = secs;
+  }
+}
+
 }  // namespace
 
 void reg::set_thread_error(const std::string& msg) { g_create_error = msg; }
@@ -1305,6 +1638,42 @@ reg_status fail(reg_ctx* c, int st, const std::string& msg) {
   }                                                                                                   \
   return REG_OK;
 
+namespace {
+
+// A context on B stacked problems of one shape (B = 1: the ordinary context).
+// Arguments are validated by the caller. Throws on failure.
+reg_ctx* create_ctx(int d, const int64_t* n, int n_t, int n_c, double beta, int reg_type, int stokes, int precision,
+                    int ckpt_every, void* cuda_stream, int batch) {
+  Grid g = make_grid(d, n, batch);
+  std::unique_ptr<reg_ctx> holder(new reg_ctx());
+  reg_ctx* c = holder.get();
+  c->d = d;
+  c->g = g;
+  c->n_t = n_t;
+  c->n_c = n_c;
+  c->beta = beta;
+  c->rtype = reg_type;
+  c->stokes = stokes;
+  c->prec = precision;
+  c->ckpt = ckpt_every;
+  c->s = (cudaStream_t)cuda_stream;
+  c->graphs = c->s != nullptr;  // a context with its own stream replays its matvec as a CUDA graph
+  for (int i = 0; i < d; ++i) c->hd *= 2.0 * M_PI / g.n[i];
+  c->bnode.resize((size_t)(n_t + 1) * n_c);
+  for (int j = 0; j <= n_t; ++j) cheb_values(n_c, (double)j / n_t, &c->bnode[(size_t)j * n_c]);
+  c->Cg.resize(n_c * n_c);
+  for (int a = 0; a < n_c; ++a)
+    for (int b = 0; b < n_c; ++b) c->Cg[a * n_c + b] = cheb_gram_entry(a, b);
+  if (!invert_small(n_c, c->Cg, c->Ci)) throw StatusError{REG_EINVAL, "singular Gram matrix"};
+  REG_CUDA(cudaMemcpy(c->Cg_dev.get(n_c * n_c), c->Cg.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
+  REG_CUDA(cudaMemcpy(c->Ci_dev.get(n_c * n_c), c->Ci.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
+  c->sp64.reset(new Spectral<double>(g, c->s));
+  if (precision == REG_MIXED) c->sp32.reset(new Spectral<float>(g, c->s));
+  return holder.release();
+}
+
+}  // namespace
+
 extern "C" {
 
 reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, int n_c, double beta, int reg_type, int stokes,
@@ -1320,43 +1689,15 @@ reg_status reg_create(reg_ctx** out, int d, const int64_t* n, int n_t, int n_c, 
   if (precision != REG_FP64 && precision != REG_MIXED) return fail(nullptr, REG_EINVAL, "bad precision");
   if (ckpt_every < 0 || (ckpt_every > 0 && n_t % ckpt_every != 0))
     return fail(nullptr, REG_EINVAL, "ckpt_every must be 0 or divide n_t");
-  reg_ctx* c = nullptr;
   try {
-    Grid g = make_grid(d, n);
-    c = new reg_ctx();
-    c->d = d;
-    c->g = g;
-    c->n_t = n_t;
-    c->n_c = n_c;
-    c->beta = beta;
-    c->rtype = reg_type;
-    c->stokes = stokes;
-    c->prec = precision;
-    c->ckpt = ckpt_every;
-    c->s = (cudaStream_t)cuda_stream;
-    c->graphs = c->s != nullptr;  // a context with its own stream replays its matvec as a CUDA graph
-    for (int i = 0; i < d; ++i) c->hd *= 2.0 * M_PI / g.n[i];
-    c->bnode.resize((size_t)(n_t + 1) * n_c);
-    for (int j = 0; j <= n_t; ++j) cheb_values(n_c, (double)j / n_t, &c->bnode[(size_t)j * n_c]);
-    c->Cg.resize(n_c * n_c);
-    for (int a = 0; a < n_c; ++a)
-      for (int b = 0; b < n_c; ++b) c->Cg[a * n_c + b] = cheb_gram_entry(a, b);
-    if (!invert_small(n_c, c->Cg, c->Ci)) throw StatusError{REG_EINVAL, "singular Gram matrix"};
-    REG_CUDA(cudaMemcpy(c->Cg_dev.get(n_c * n_c), c->Cg.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
-    REG_CUDA(cudaMemcpy(c->Ci_dev.get(n_c * n_c), c->Ci.data(), n_c * n_c * sizeof(double), cudaMemcpyHostToDevice));
-    c->sp64.reset(new Spectral<double>(g, c->s));
-    if (precision == REG_MIXED) c->sp32.reset(new Spectral<float>(g, c->s));
+    *out = create_ctx(d, n, n_t, n_c, beta, reg_type, stokes, precision, ckpt_every, cuda_stream, 1);
   } catch (const StatusError& e) {
-    delete c;
     return fail(nullptr, e.status, e.what);
   } catch (const CudaError& e) {
-    delete c;
     return fail(nullptr, e.code == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA, e.what);
   } catch (const std::bad_alloc&) {
-    delete c;
     return fail(nullptr, REG_ENOMEM, "host allocation failed");
   }
-  *out = c;
   return REG_OK;
 }
 
@@ -1671,6 +2012,119 @@ void reg_solve_opts_default(reg_solve_opts* o) {
   o->step_memory = 1;
   o->stop_rule = REG_STOP_GRAD_REL;
   o->tau_J = 1e-3;
+}
+
+reg_status reg_solve_lockstep(const reg_problem* problems, int count, int precision, const reg_solve_opts* opts,
+                              reg_solve_report* reports, int max_stack) {
+  if (!problems || count < 0 || max_stack < 0) {
+    g_create_error = "reg_solve_lockstep: bad arguments";
+    return REG_EINVAL;
+  }
+  if (count == 0) return REG_OK;
+  if (precision != REG_FP64 && precision != REG_MIXED) {
+    g_create_error = "reg_solve_lockstep: bad precision";
+    return REG_EINVAL;
+  }
+  reg_solve_opts o;
+  reg_solve_opts_default(&o);
+  if (opts) o = *opts;
+  // groups of one shape and time discretisation, in order of first appearance
+  using GKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int>;
+  std::map<GKey, std::vector<int>> groups;
+  std::vector<GKey> order;
+  for (int i = 0; i < count; ++i) {
+    const reg_problem& p = problems[i];
+    if ((p.d != 2 && p.d != 3) || p.n_t < 1 || p.n_c < 1 || p.n_c > 16 || !(p.beta > 0.0) ||
+        (p.reg_type != REG_H1 && p.reg_type != REG_H2) || (p.stokes != 0 && p.stokes != 1) || !p.m_T || !p.m_R ||
+        !p.v) {
+      g_create_error = "reg_solve_lockstep: problem " + std::to_string(i) + " is invalid";
+      return REG_EINVAL;
+    }
+    GKey k(p.d, p.n[0], p.n[1], p.d == 3 ? p.n[2] : 1, p.n_t, p.n_c, p.reg_type, p.stokes);
+    if (!groups.count(k)) order.push_back(k);
+    auto& list = groups[k];
+    list.push_back(i);
+  }
+  // stacks of at most max_stack problems
+  std::vector<std::vector<int>> stacks;
+  for (const GKey& k : order) {
+    const auto& list = groups[k];
+    const int cap = max_stack > 0 ? max_stack : (int)list.size();
+    for (size_t a = 0; a < list.size(); a += cap)
+      stacks.emplace_back(list.begin() + a, list.begin() + std::min(list.size(), a + cap));
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    g_create_error = "reg_solve_lockstep: no CUDA device";
+    return REG_ECUDA;
+  }
+  std::vector<int> status(stacks.size(), REG_OK);
+  std::vector<std::string> errors(stacks.size());
+  auto run = [&](size_t si) {
+    cudaSetDevice(dev);
+    const std::vector<int>& ids = stacks[si];
+    const reg_problem& p0 = problems[ids[0]];
+    const int B = (int)ids.size();
+    cudaStream_t st = nullptr;
+    reg_ctx* c = nullptr;
+    try {
+      REG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      c = create_ctx(p0.d, p0.n, p0.n_t, p0.n_c, p0.beta, p0.reg_type, p0.stokes, precision, 0, st, B);
+      const long N1 = c->g.N1, N = c->N();
+      const int K = c->n_c * c->d;
+      c->betas.resize(B);
+      for (int q = 0; q < B; ++q) c->betas[q] = problems[ids[q]].beta;
+      REG_CUDA(cudaMemcpyAsync(c->betas_dev.get(B), c->betas.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+      double* mT = c->mT.get(N);
+      double* mR = c->mR.get(N);
+      double* v = c->sv_v.get(c->ncdN());
+      for (int q = 0; q < B; ++q) {
+        const reg_problem& p = problems[ids[q]];
+        REG_CUDA(cudaMemcpyAsync(mT + q * N1, p.m_T, N1 * sizeof(double), cudaMemcpyDefault, st));
+        REG_CUDA(cudaMemcpyAsync(mR + q * N1, p.m_R, N1 * sizeof(double), cudaMemcpyDefault, st));
+        for (int k = 0; k < K; ++k)
+          REG_CUDA(cudaMemcpyAsync(v + ((long)k * B + q) * N1, p.v + (long)k * N1, N1 * sizeof(double),
+                                   cudaMemcpyDefault, st));
+      }
+      c->have_images = true;
+      std::vector<reg_solve_report> R(B);
+      solve_lockstep(c, v, o, R.data());
+      for (int q = 0; q < B; ++q) {
+        const reg_problem& p = problems[ids[q]];
+        for (int k = 0; k < K; ++k)
+          REG_CUDA(cudaMemcpyAsync(p.v + (long)k * N1, v + ((long)k * B + q) * N1, N1 * sizeof(double),
+                                   cudaMemcpyDefault, st));
+        if (reports) reports[ids[q]] = R[q];
+        if (R[q].status != REG_OK && R[q].status != REG_EMAXIT && status[si] == REG_OK) {
+          status[si] = R[q].status;
+          errors[si] = "problem " + std::to_string(ids[q]) + " ended with status " + std::to_string(R[q].status);
+        }
+      }
+      REG_CUDA(cudaStreamSynchronize(st));
+    } catch (const StatusError& e) {
+      status[si] = e.status;
+      errors[si] = e.what;
+    } catch (const CudaError& e) {
+      status[si] = e.code == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA;
+      errors[si] = e.what;
+    } catch (const std::bad_alloc&) {
+      status[si] = REG_ENOMEM;
+      errors[si] = "host allocation failed";
+    }
+    delete c;
+    if (st) cudaStreamDestroy(st);
+  };
+  // the stacks run concurrently, one thread and stream each
+  std::vector<std::thread> pool;
+  for (size_t si = 0; si < stacks.size(); ++si) pool.emplace_back(run, si);
+  for (auto& t : pool) t.join();
+  for (size_t si = 0; si < stacks.size(); ++si)
+    if (status[si] != REG_OK) {
+      g_create_error = "reg_solve_lockstep: " + errors[si];
+      return (reg_status)status[si];
+    }
+  return REG_OK;
 }
 
 reg_status reg_solve(reg_ctx* ctx, double* v_inout, const reg_solve_opts* opts, reg_solve_report* report) {

@@ -161,13 +161,14 @@ struct GridArgs {
   int d;
   int n[3];
   int M;
-  long Nc;
+  long Nc;   // all stacked problems
+  long Nc1;  // one problem
 };
-__device__ inline long encode_neg(const ModeIdx& m, const GridArgs& g) {
-  // index of -k' on the slot-0 plane
+// index of -k' on the slot-0 plane of the problem that holds mode q
+__device__ inline long encode_neg(long q0, const ModeIdx& m, const GridArgs& g) {
   long q = 0;
   for (int a = 0; a < g.d - 1; ++a) q = q * g.n[a] + ((g.n[a] - m.j[a]) % g.n[a]);
-  return q * g.M;
+  return (q0 / g.Nc1) * g.Nc1 + q * g.M;
 }
 __device__ inline double masked_k(const ModeIdx& m, const GridArgs& g, int a) {
   if (a == g.d - 1) return (double)m.j[a];  // slot 0 -> 0 for both DC and Nyquist halves
@@ -224,9 +225,11 @@ __device__ inline double sym_pow(double kk, int reg) { return reg == 1 ? kk : kk
 constexpr int kMaxNc = 16;
 
 __global__ void k_spec_tail(const double2* __restrict__ V, const double2* __restrict__ F, double2* __restrict__ out,
-                            GridArgs g, int nc, double beta, const double* __restrict__ Cg, int reg, int stokes) {
+                            GridArgs g, int nc, double beta, const double* __restrict__ Cg, int reg, int stokes,
+                            const double* __restrict__ betas) {
   long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.Nc) return;
+  if (betas) beta = betas[q / g.Nc1];
   const int d = g.d;
   const long Nc = g.Nc;
   ModeIdx m = decode(q, d, g.n, g.M);
@@ -238,7 +241,7 @@ __global__ void k_spec_tail(const double2* __restrict__ V, const double2* __rest
     double a0 = sym_pow(kk, reg), aN = sym_pow(kk + 0.25 * (double)g.n[d - 1] * g.n[d - 1], reg);
     alpha = 0.5 * (a0 + aN);
     delta = 0.5 * (a0 - aN);
-    qn = encode_neg(m, g);
+    qn = encode_neg(q, m, g);
   } else {
     alpha = sym_pow(kk + (double)kz * kz, reg);
     delta = 0.0;
@@ -280,9 +283,10 @@ __global__ void k_spec_tail(const double2* __restrict__ V, const double2* __rest
 }
 
 __global__ void k_spec_precond(const double2* __restrict__ R, double2* __restrict__ out, GridArgs g, int nc,
-                               double beta, const double* __restrict__ Ci, int reg) {
+                               double beta, const double* __restrict__ Ci, int reg, const double* __restrict__ betas) {
   long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= g.Nc) return;
+  if (betas) beta = betas[q / g.Nc1];
   const int d = g.d;
   const long Nc = g.Nc;
   ModeIdx m = decode(q, d, g.n, g.M);
@@ -292,11 +296,11 @@ __global__ void k_spec_precond(const double2* __restrict__ R, double2* __restric
   long qn = q;
   if (kz == 0) {
     double a0 = sym_pow(kk, reg), aN = sym_pow(kk + 0.25 * (double)g.n[d - 1] * g.n[d - 1], reg);
-    double s0 = (q == 0) ? 1.0 : 1.0 / (beta * a0);  // k = 0: the inverse is replaced by one
+    double s0 = (q % g.Nc1 == 0) ? 1.0 : 1.0 / (beta * a0);  // k = 0: the inverse is replaced by one
     double sN = 1.0 / (beta * aN);
     alpha = 0.5 * (s0 + sN);
     delta = 0.5 * (s0 - sN);
-    qn = encode_neg(m, g);
+    qn = encode_neg(q, m, g);
   } else {
     alpha = 1.0 / (beta * sym_pow(kk + (double)kz * kz, reg));
     delta = 0.0;
@@ -328,7 +332,7 @@ __global__ void k_spec_gauss(double2* __restrict__ U, double2* __restrict__ out,
   if (kz == 0) {
     double g0 = exp(-0.5 * s2 * kk), gN = exp(-0.5 * s2 * (kk + 0.25 * (double)g.n[d - 1] * g.n[d - 1]));
     double alpha = 0.5 * (g0 + gN), delta = 0.5 * (g0 - gN);
-    double2 vn = U[encode_neg(m, g)];
+    double2 vn = U[encode_neg(q, m, g)];
     out[q] = make_double2(alpha * v.x + delta * vn.x, alpha * v.y - delta * vn.y);
   } else {
     double gk = exp(-0.5 * s2 * (kk + (double)kz * kz));
@@ -342,6 +346,7 @@ GridArgs args(const Grid& g) {
   for (int i = 0; i < 3; ++i) a.n[i] = g.n[i];
   a.M = g.M;
   a.Nc = g.Nc;
+  a.Nc1 = g.Nc / g.B;
   return a;
 }
 
@@ -450,8 +455,9 @@ unsigned blocks_for(long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs)
 
 }  // namespace
 
-Grid make_grid(int d, const int64_t* n) {
+Grid make_grid(int d, const int64_t* n, int batch) {
   Grid g;
+  if (batch < 1) throw StatusError{1, "batch must be >= 1"};
   if (d != 2 && d != 3) throw StatusError{1, "d must be 2 or 3"};
   g.d = d;
   g.N = 1;
@@ -462,6 +468,9 @@ Grid make_grid(int d, const int64_t* n) {
     g.n[a] = (int)k;
     g.N *= k;
   }
+  g.N1 = g.N;
+  g.B = batch;
+  g.N *= batch;
   g.L = g.n[d - 1];
   g.M = g.L / 2;
   g.Nc = g.N / 2;
@@ -616,15 +625,15 @@ template class Spectral<float>;
 template class Spectral<double>;
 
 void spec_tail(const Grid& g, cudaStream_t s, const double2* V, const double2* F, double2* out, int nc, double beta,
-               const double* Cg_dev, int reg, int stokes) {
+               const double* Cg_dev, int reg, int stokes, const double* betas) {
   if (nc > kMaxNc) throw StatusError{1, "n_c too large"};
-  k_spec_tail<<<blocks_for(g.Nc), 256, 0, s>>>(V, F, out, args(g), nc, beta, Cg_dev, reg, stokes);
+  k_spec_tail<<<blocks_for(g.Nc), 256, 0, s>>>(V, F, out, args(g), nc, beta, Cg_dev, reg, stokes, betas);
   REG_LAUNCH();
 }
 
 void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out, int nc, double beta,
-                  const double* Ci_dev, int reg) {
-  k_spec_precond<<<blocks_for(g.Nc), 256, 0, s>>>(R, out, args(g), nc, beta, Ci_dev, reg);
+                  const double* Ci_dev, int reg, const double* betas) {
+  k_spec_precond<<<blocks_for(g.Nc), 256, 0, s>>>(R, out, args(g), nc, beta, Ci_dev, reg, betas);
   REG_LAUNCH();
 }
 

@@ -183,6 +183,8 @@ _SIGNATURES = {
                             _vp, _vp, _vp],
     "reg_solve_batched": [ctypes.POINTER(ProblemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(SolveOpts),
                           ctypes.POINTER(SolveReport), ctypes.c_int],
+    "reg_solve_lockstep": [ctypes.POINTER(ProblemC), ctypes.c_int, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                           ctypes.POINTER(SolveReport), ctypes.c_int],
     "reg_profile_begin": [_vp, ctypes.c_uint],
     "reg_profile_end": [_vp, _vp, _vp, _vp],
 }
@@ -210,13 +212,7 @@ def precond_noalloc(n, n_c, beta, reg, r, z, stream=None):
         raise RegError(st, L.reg_last_error(None).decode())
 
 
-def solve_batched(problems, precision=REG_MIXED, workers=8, **opts):
-    """Solve independent problems concurrently (reg_solve_batched).
-
-    problems: list of dicts with keys n, n_t, n_c, beta, reg, stokes, mT, mR, v
-    (arrays as accepted by Registration; v is updated in place). Returns the
-    list of report dicts in the order of `problems`."""
-    L = load()
+def _problem_array(problems):
     arr = (ProblemC * len(problems))()
     keep = []
     for i, p in enumerate(problems):
@@ -228,9 +224,34 @@ def solve_batched(problems, precision=REG_MIXED, workers=8, **opts):
         arr[i] = ProblemC(len(n), (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))), int(p["n_t"]),
                           int(p.get("n_c", 1)), float(p["beta"]), int(p.get("reg", REG_H1)),
                           int(bool(p.get("stokes", False))), a, b, c)
+    return arr, keep
+
+
+def solve_batched(problems, precision=REG_MIXED, workers=8, **opts):
+    """Solve independent problems concurrently (reg_solve_batched).
+
+    problems: list of dicts with keys n, n_t, n_c, beta, reg, stokes, mT, mR, v
+    (arrays as accepted by Registration; v is updated in place). Returns the
+    list of report dicts in the order of `problems`."""
+    L = load()
+    arr, keep = _problem_array(problems)
     o = SolveOpts.make(L, opts)
     reps = (SolveReport * len(problems))()
     st = L.reg_solve_batched(arr, len(problems), int(precision), ctypes.byref(o), reps, int(workers))
+    if st not in (REG_OK, REG_EMAXIT):
+        raise RegError(st, L.reg_last_error(None).decode())
+    return [r.as_dict() for r in reps]
+
+
+def solve_lockstep(problems, precision=REG_MIXED, max_stack=0, **opts):
+    """Lockstep batched solve (reg_solve_lockstep): problems of one shape are
+    stacked and iterated together. Same arguments and result as solve_batched;
+    a failed stack raises, with the reports of the others lost."""
+    L = load()
+    arr, keep = _problem_array(problems)
+    o = SolveOpts.make(L, opts)
+    reps = (SolveReport * len(problems))()
+    st = L.reg_solve_lockstep(arr, len(problems), int(precision), ctypes.byref(o), reps, int(max_stack))
     if st not in (REG_OK, REG_EMAXIT):
         raise RegError(st, L.reg_last_error(None).decode())
     return [r.as_dict() for r in reps]
