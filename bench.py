@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--pairs", type=int, default=256)
     p.add_argument("--batch-sample", type=int, default=256)
     p.add_argument("--batch-mode", default="lockstep", choices=["lockstep", "executor"])
+    p.add_argument("--max-stack", type=int, default=0, help="problems per lockstep stack (0: one per shape)")
     p.add_argument("--workers", type=int, default=8)
     return p.parse_args()
 
@@ -254,6 +255,9 @@ def batch_pairs(count):
     return pairs
 
 
+MAX_STACK = 0  # problems per lockstep stack (0: one stack per shape)
+
+
 def solve_pairs(pairs, workers, mode="lockstep"):
     """reference images by the library's own transport, then one batched solve
     (mode "lockstep": reg_solve_lockstep; "executor": reg_solve_batched with
@@ -278,7 +282,7 @@ def solve_pairs(pairs, workers, mode="lockstep"):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if mode == "lockstep":
-        reps = lib.solve_lockstep(probs, precision=lib.REG_MIXED, grad_rtol=1e-2)
+        reps = lib.solve_lockstep(probs, precision=lib.REG_MIXED, max_stack=MAX_STACK, grad_rtol=1e-2)
     else:
         reps = lib.solve_batched(probs, precision=lib.REG_MIXED, workers=workers, grad_rtol=1e-2)
     torch.cuda.synchronize()
@@ -524,7 +528,9 @@ def run_ours(args):
 
 
 def main():
+    global MAX_STACK
     args = parse()
+    MAX_STACK = args.max_stack
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

@@ -17,6 +17,7 @@
 #include <thread>
 #include <tuple>
 #include <memory>
+#include <numeric>
 #include <new>
 #include <string>
 #include <vector>
@@ -1373,8 +1374,26 @@ void cfl_seg(reg_ctx* c, const double* v, std::vector<double>& out) {
   }
 }
 
-void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report* R) {
-  auto t0 = std::chrono::steady_clock::now();
+// Stacks of at least this many problems are rebuilt from their running
+// problems once half of them have stopped.
+constexpr int kRestackMin = 8;
+
+// Per-problem state of a lockstep solve that outlives one stack (restacking).
+struct LockState {
+  std::vector<int> active, k;
+  std::vector<double> J, g02, amem;
+  std::vector<reg_solve_report> R;
+  explicit LockState(int n) : active(n, 1), k(n, 0), J(n, 0.0), g02(n, 0.0), amem(n, 1.0), R(n) {
+    for (auto& r : R) std::memset(&r, 0, sizeof(r));
+  }
+};
+
+// Runs the lockstep outer loop on the stack in c; slot q of the stack is
+// problem S[slot[q]]. Returns true when it stops early so that the caller can
+// restack the remaining problems: at the start of an outer iteration, when at
+// most half of a stack of at least `restack_min` problems is still running.
+bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S, const std::vector<int>& slot,
+                    bool resume, int restack_min) {
   const int B = c->g.B;
   const long n = c->ncdN();
   double* g = c->sv_g.get(n);
@@ -1386,29 +1405,72 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
   double* vt = c->sv_vt.get(n);
   Seg sg(c, c->n_c * c->d);
   const long maxit = o.pcg_maxit > 0 ? o.pcg_maxit : n / B;
-  std::vector<double> dist, regt, J(B), ginf, g2, g02, zero(B, 0.0), one(B, 1.0), tmp, tmp2;
-  std::vector<int> active(B, 1), k(B, 0);
-  std::vector<double> amem(B, 1.0);
-  for (int q = 0; q < B; ++q) std::memset(&R[q], 0, sizeof(reg_solve_report));
+  std::vector<double> dist, regt, J(B), ginf, g2, g02(B), zero(B, 0.0), one(B, 1.0), tmp, tmp2;
+  std::vector<int> active(B), k(B);
+  std::vector<double> amem(B);
+  std::vector<reg_solve_report*> Rp(B);
+  for (int q = 0; q < B; ++q) {
+    active[q] = S.active[slot[q]];
+    k[q] = S.k[slot[q]];
+    amem[q] = S.amem[slot[q]];
+    g02[q] = S.g02[slot[q]];
+    Rp[q] = &S.R[slot[q]];
+  }
+  struct Sync {  // the per-problem state back into S on every exit
+    LockState& S;
+    const std::vector<int>& slot;
+    std::vector<int>& active;
+    std::vector<int>& k;
+    std::vector<double>& J;
+    std::vector<double>& amem;
+    ~Sync() {
+      for (size_t q = 0; q < slot.size(); ++q) {
+        S.active[slot[q]] = active[q];
+        S.k[slot[q]] = k[q];
+        S.J[slot[q]] = J[q];
+        S.amem[slot[q]] = amem[q];
+      }
+    }
+  } sync{S, slot, active, k, J, amem};
+  auto R = [&](int q) -> reg_solve_report& { return *Rp[q]; };
   auto finite_or_fail = [&](int q, double x) {
     if (active[q] && !std::isfinite(x)) {
       active[q] = 0;
-      R[q].status = REG_ENONFINITE;
+      R(q).status = REG_ENONFINITE;
+    }
+  };
+  // final measures of the problems that have stopped (all, at the end)
+  auto finalize = [&](bool all) {
+    std::vector<double> base(B), cf;
+    Seg one1(c, 1);
+    seg_sqdiff(c->mT.p, c->mR.p, 1, B, c->g.N1, one1.scr, c->s, base.data());
+    cfl_seg(c, v, cf);
+    for (int q = 0; q < B; ++q) {
+      if (!all && active[q]) continue;
+      R(q).outer = k[q];
+      R(q).J = J[q];
+      R(q).dist_rel = base[q] > 0 ? (2.0 * dist[q] / c->hd) / base[q] : 0.0;
+      R(q).cfl = cf[q];
     }
   };
   gradient_seg(c, v, g, dist, regt);
-  sg.maxabs(g, ginf);
-  sg.dot(g, g, tmp);
-  sg.maxabs(v, tmp2);
-  for (int q = 0; q < B; ++q) {
-    J[q] = dist[q] + regt[q];
-    R[q].n_pde = 2;
-    R[q].J0 = J[q];
-    R[q].g0_inf = ginf[q];
-    R[q].v_inf = tmp2[q];
-    R[q].alpha_mem = 1.0;
-    g02.push_back(std::sqrt(tmp[q]));
-    finite_or_fail(q, J[q] + tmp[q]);
+  if (!resume) {
+    sg.maxabs(g, ginf);
+    sg.dot(g, g, tmp);
+    sg.maxabs(v, tmp2);
+    for (int q = 0; q < B; ++q) {
+      J[q] = dist[q] + regt[q];
+      R(q).n_pde = 2;
+      R(q).J0 = J[q];
+      R(q).g0_inf = ginf[q];
+      R(q).v_inf = tmp2[q];
+      R(q).alpha_mem = 1.0;
+      g02[q] = std::sqrt(tmp[q]);
+      S.g02[slot[q]] = g02[q];
+      finite_or_fail(q, J[q] + tmp[q]);
+    }
+  } else {
+    for (int q = 0; q < B; ++q) J[q] = dist[q] + regt[q];
   }
   for (;;) {
     sg.maxabs(g, ginf);
@@ -1418,17 +1480,21 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
     for (int q = 0; q < B; ++q) {
       g2[q] = std::sqrt(tmp[q]);
       if (!active[q]) continue;
-      R[q].g_inf = ginf[q];
-      R[q].J = J[q];
+      R(q).g_inf = ginf[q];
+      R(q).J = J[q];
       bool maxed = false;
-      if (stop_test(o, R[q], k[q], ginf[q], maxed)) {
+      if (stop_test(o, R(q), k[q], ginf[q], maxed)) {
         active[q] = 0;
-        R[q].status = maxed ? REG_EMAXIT : REG_OK;
+        R(q).status = maxed ? REG_EMAXIT : REG_OK;
       } else {
         ++live;
       }
     }
     if (!live) break;
+    if (B >= restack_min && 2 * live <= B) {  // restack the running problems
+      finalize(false);
+      return true;
+    }
     std::vector<double> act(B);
     for (int q = 0; q < B; ++q) act[q] = active[q] ? 1.0 : 0.0;
     if (o.method == REG_METHOD_PICARD) {
@@ -1464,9 +1530,9 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
         bool any_copy = false;
         for (int q = 0; q < B; ++q) {
           if (!on[q]) continue;
-          R[q].matvecs += 1;
-          R[q].n_pde += 2;
-          R[q].pcg_iters += 1;
+          R(q).matvecs += 1;
+          R(q).n_pde += 2;
+          R(q).pcg_iters += 1;
           finite_or_fail(q, pHp[q]);
           if (!active[q]) {
             on[q] = 0;
@@ -1512,11 +1578,11 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
           if (!active[q] || cf[q] <= o.cfl_max) continue;
           if (++halvings[q] > 30) {
             active[q] = 0;
-            R[q].status = REG_ECFL;
+            R(q).status = REG_ECFL;
             h[q] = 0.0;  // no step
           } else {
             h[q] = 0.5;
-            R[q].cfl_halvings += 1;
+            R(q).cfl_halvings += 1;
           }
           any = true;
         }
@@ -1542,8 +1608,8 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
       objective_seg(c, vt, d2, r2);
       for (int q = 0; q < B; ++q) {
         if (!searching[q]) continue;
-        R[q].ls_trials += 1;
-        R[q].n_pde += 1;
+        R(q).ls_trials += 1;
+        R(q).n_pde += 1;
         Jt[q] = d2[q] + r2[q];
         if (std::isfinite(Jt[q]) && Jt[q] <= J[q] + o.armijo_c1 * alpha[q] * slope[q]) {
           searching[q] = 0;
@@ -1556,14 +1622,14 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
     for (int q = 0; q < B; ++q)
       if (searching[q]) {  // no sufficient decrease: the problem keeps its iterate
         active[q] = 0;
-        R[q].status = REG_ELINESEARCH;
+        R(q).status = REG_ELINESEARCH;
         alpha[q] = 0.0;
       }
     for (int q = 0; q < B; ++q) {
       if (!active[q]) alpha[q] = 0.0;
       if (active[q] && o.method == REG_METHOD_PICARD && o.step_memory)
         amem[q] = (alpha[q] == 1.0) ? 2.0 * amem[q] : amem[q] * alpha[q];
-      R[q].alpha_mem = amem[q];
+      R(q).alpha_mem = amem[q];
     }
     sg.comb(one, v, alpha, s, vt);
     sg.comb(one, vt, std::vector<double>(B, -1.0), v, r);  // v_k - v_{k-1}
@@ -1574,35 +1640,21 @@ void solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_re
     std::vector<int> stepped = active;
     for (int q = 0; q < B; ++q)
       if (stepped[q]) {
-        R[q].dv_inf = dv[q];
-        R[q].v_inf = vin[q];
-        R[q].J_prev = J[q];
+        R(q).dv_inf = dv[q];
+        R(q).v_inf = vin[q];
+        R(q).J_prev = J[q];
       }
     gradient_seg(c, v, g, dist, regt);
     for (int q = 0; q < B; ++q) {
       if (!stepped[q]) continue;
       J[q] = dist[q] + regt[q];
-      R[q].n_pde += 2;
+      R(q).n_pde += 2;
       k[q] += 1;
       finite_or_fail(q, J[q]);
     }
   }
-  // final measures per problem
-  std::vector<double> base(B), cf;
-  {
-    Seg one1(c, 1);
-    seg_sqdiff(c->mT.p, c->mR.p, 1, B, c->g.N1, one1.scr, c->s, base.data());
-  }
-  cfl_seg(c, v, cf);
-  REG_CUDA(cudaStreamSynchronize(c->s));
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  for (int q = 0; q < B; ++q) {
-    R[q].outer = k[q];
-    R[q].J = J[q];
-    R[q].dist_rel = base[q] > 0 ? (2.0 * dist[q] / c->hd) / base[q] : 0.0;
-    R[q].cfl = cf[q];
-    R[q].seconds = secs;
-  }
+  finalize(true);
+  return false;
 }
 
 }  // namespace
@@ -2065,43 +2117,62 @@ reg_status reg_solve_lockstep(const reg_problem* problems, int count, int precis
     cudaSetDevice(dev);
     const std::vector<int>& ids = stacks[si];
     const reg_problem& p0 = problems[ids[0]];
-    const int B = (int)ids.size();
     cudaStream_t st = nullptr;
     reg_ctx* c = nullptr;
+    auto t0 = std::chrono::steady_clock::now();
     try {
       REG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-      c = create_ctx(p0.d, p0.n, p0.n_t, p0.n_c, p0.beta, p0.reg_type, p0.stokes, precision, 0, st, B);
-      const long N1 = c->g.N1, N = c->N();
-      const int K = c->n_c * c->d;
-      c->betas.resize(B);
-      for (int q = 0; q < B; ++q) c->betas[q] = problems[ids[q]].beta;
-      REG_CUDA(cudaMemcpyAsync(c->betas_dev.get(B), c->betas.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
-      double* mT = c->mT.get(N);
-      double* mR = c->mR.get(N);
-      double* v = c->sv_v.get(c->ncdN());
-      for (int q = 0; q < B; ++q) {
-        const reg_problem& p = problems[ids[q]];
-        REG_CUDA(cudaMemcpyAsync(mT + q * N1, p.m_T, N1 * sizeof(double), cudaMemcpyDefault, st));
-        REG_CUDA(cudaMemcpyAsync(mR + q * N1, p.m_R, N1 * sizeof(double), cudaMemcpyDefault, st));
-        for (int k = 0; k < K; ++k)
-          REG_CUDA(cudaMemcpyAsync(v + ((long)k * B + q) * N1, p.v + (long)k * N1, N1 * sizeof(double),
-                                   cudaMemcpyDefault, st));
+      LockState S((int)ids.size());
+      std::vector<int> slot(ids.size());
+      std::iota(slot.begin(), slot.end(), 0);
+      bool resume = false;
+      for (;;) {
+        // a stack of the problems in `slot` (positions in ids), loaded from the callers' arrays
+        const int B = (int)slot.size();
+        c = create_ctx(p0.d, p0.n, p0.n_t, p0.n_c, p0.beta, p0.reg_type, p0.stokes, precision, 0, st, B);
+        const long N1 = c->g.N1, N = c->N();
+        const int K = c->n_c * c->d;
+        c->betas.resize(B);
+        for (int q = 0; q < B; ++q) c->betas[q] = problems[ids[slot[q]]].beta;
+        REG_CUDA(cudaMemcpyAsync(c->betas_dev.get(B), c->betas.data(), B * sizeof(double), cudaMemcpyHostToDevice, st));
+        double* mT = c->mT.get(N);
+        double* mR = c->mR.get(N);
+        double* v = c->sv_v.get(c->ncdN());
+        for (int q = 0; q < B; ++q) {
+          const reg_problem& p = problems[ids[slot[q]]];
+          REG_CUDA(cudaMemcpyAsync(mT + q * N1, p.m_T, N1 * sizeof(double), cudaMemcpyDefault, st));
+          REG_CUDA(cudaMemcpyAsync(mR + q * N1, p.m_R, N1 * sizeof(double), cudaMemcpyDefault, st));
+          for (int k = 0; k < K; ++k)
+            REG_CUDA(cudaMemcpyAsync(v + ((long)k * B + q) * N1, p.v + (long)k * N1, N1 * sizeof(double),
+                                     cudaMemcpyDefault, st));
+        }
+        c->have_images = true;
+        const bool more = solve_lockstep(c, v, o, S, slot, resume, kRestackMin);
+        for (int q = 0; q < B; ++q) {  // iterates back to the callers' arrays (final for stopped problems)
+          const reg_problem& p = problems[ids[slot[q]]];
+          for (int k = 0; k < K; ++k)
+            REG_CUDA(cudaMemcpyAsync(p.v + (long)k * N1, v + ((long)k * B + q) * N1, N1 * sizeof(double),
+                                     cudaMemcpyDefault, st));
+        }
+        REG_CUDA(cudaStreamSynchronize(st));
+        delete c;
+        c = nullptr;
+        if (!more) break;
+        std::vector<int> live;
+        for (int q : slot)
+          if (S.active[q]) live.push_back(q);
+        slot.swap(live);
+        resume = true;
       }
-      c->have_images = true;
-      std::vector<reg_solve_report> R(B);
-      solve_lockstep(c, v, o, R.data());
-      for (int q = 0; q < B; ++q) {
-        const reg_problem& p = problems[ids[q]];
-        for (int k = 0; k < K; ++k)
-          REG_CUDA(cudaMemcpyAsync(p.v + (long)k * N1, v + ((long)k * B + q) * N1, N1 * sizeof(double),
-                                   cudaMemcpyDefault, st));
-        if (reports) reports[ids[q]] = R[q];
-        if (R[q].status != REG_OK && R[q].status != REG_EMAXIT && status[si] == REG_OK) {
-          status[si] = R[q].status;
-          errors[si] = "problem " + std::to_string(ids[q]) + " ended with status " + std::to_string(R[q].status);
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      for (size_t q = 0; q < ids.size(); ++q) {
+        S.R[q].seconds = secs;
+        if (reports) reports[ids[q]] = S.R[q];
+        if (S.R[q].status != REG_OK && S.R[q].status != REG_EMAXIT && status[si] == REG_OK) {
+          status[si] = S.R[q].status;
+          errors[si] = "problem " + std::to_string(ids[q]) + " ended with status " + std::to_string(S.R[q].status);
         }
       }
-      REG_CUDA(cudaStreamSynchronize(st));
     } catch (const StatusError& e) {
       status[si] = e.status;
       errors[si] = e.what;

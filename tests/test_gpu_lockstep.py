@@ -75,3 +75,22 @@ def test_lockstep_rejects_invalid_problems(batch):
     with pytest.raises(lib.RegError) as e:
         lib.solve_lockstep(probs, lib.REG_FP64)
     assert e.value.status == lib.REG_EINVAL
+
+
+def test_lockstep_restacks_running_problems():
+    # 12 pairs of one shape: once half of them have stopped the stack is
+    # rebuilt from the running ones; every problem still takes its own iterates
+    pairs = synth.batch_2d(count=12, seed=78, sizes=(32,), ratio=(1,), n_t=8)
+    for i, p in enumerate(pairs):
+        p["mR"] = O.Problem(p["n"], 16).state((0.5 + 0.1 * i) * p["v_true"], p["mT"])[-1]
+    probs = problems_of(pairs)
+    reps = lib.solve_lockstep(probs, lib.REG_FP64, grad_rtol=1e-4)
+    outers = []
+    for p, q, r in zip(pairs, probs, reps):
+        v1, r1 = single(p, lib.REG_FP64, grad_rtol=1e-4)
+        for k in ("outer", "pcg_iters", "ls_trials", "status"):
+            assert r[k] == r1[k], (k, r[k], r1[k])
+        assert rel(q["v"], v1) < 1e-9
+        assert abs(r["J"] - r1["J"]) <= 1e-11 * r1["J"] and abs(r["dist_rel"] - r1["dist_rel"]) <= 1e-9
+        outers.append(r["outer"])
+    assert len(set(outers)) > 1  # the problems stop at different iterations
