@@ -35,13 +35,17 @@ template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s)
 
 // exp(-2 pi i q/16) for compile-time q in [0,16): the 16th roots of unity.
 // cos(pi/8) and sin(pi/8) written out; sqrt(1/2) likewise.
+// The constants are rounded to T at compile time, so a single-precision
+// butterfly issues no double-precision conversion.
 template <typename T, int q> __device__ __forceinline__ cx<T> root16() {
-  constexpr double c1 = 0.92387953251128675613;  // cos(pi/8)
-  constexpr double s1 = 0.38268343236508977173;  // sin(pi/8)
-  constexpr double h = 0.70710678118654752440;   // sqrt(1/2)
-  constexpr double re[16] = {1, c1, h, s1, 0, -s1, -h, -c1, -1, -c1, -h, -s1, 0, s1, h, c1};
-  constexpr double im[16] = {0, -s1, -h, -c1, -1, -c1, -h, -s1, 0, s1, h, c1, 1, c1, h, s1};
-  return mk<cx<T>>((T)re[q], (T)im[q]);
+  constexpr T c1 = (T)0.92387953251128675613;  // cos(pi/8)
+  constexpr T s1 = (T)0.38268343236508977173;  // sin(pi/8)
+  constexpr T h = (T)0.70710678118654752440;   // sqrt(1/2)
+  constexpr T o = (T)1, z = (T)0;
+  constexpr T re[16] = {o, c1, h, s1, z, -s1, -h, -c1, -o, -c1, -h, -s1, z, s1, h, c1};
+  constexpr T im[16] = {z, -s1, -h, -c1, -o, -c1, -h, -s1, z, s1, h, c1, o, c1, h, s1};
+  constexpr T a = re[q], b = im[q];
+  return mk<cx<T>>(a, b);
 }
 
 // o * exp(-2 pi i k / R) with compile-time k, R <= 16; trivial roots skip the multiply.

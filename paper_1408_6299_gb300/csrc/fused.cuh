@@ -23,6 +23,11 @@ namespace fused {
 constexpr int kThreads = 256;
 
 __host__ __device__ inline long kmask_l(long j, long n) { return j == n / 2 ? 0 : (j < n / 2 ? j : j - n); }
+// the same for an index m < L held exactly in T (no integer conversion per element)
+template <typename T, int L>
+__device__ __forceinline__ T kmask_f(T m) {
+  return m < (T)(L / 2) ? m : (m == (T)(L / 2) ? (T)0 : m - (T)L);
+}
 
 template <typename T, int NF>
 struct RowsIn {
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(kThreads) k_cols_deriv(const cx<T>* in, cx<T>*
   const T sc = (T)1 / (T)L;
   for (int e = threadIdx.x; e < L * TC; e += kThreads) {
     int j = e / TC;
-    T k = (T)kmask_l(j, L) * sc;
+    T k = kmask_f<T, L>((T)j) * sc;
     C z = buf[e];
     buf[e] = cconj(mk<C>(-k * z.y, k * z.x));  // conjugated: the inverse runs as a forward FFT
   }
@@ -457,7 +462,6 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
   using C = cx<T>;
   constexpr int Q0 = L / R0;  // tasks per column of the radix-R0 stages
   constexpr int Q1 = R0;      // tasks per column of the radix-R1 stages (L / R1)
-  constexpr int NT = TC * (Q0 > Q1 ? Q0 : Q1);
   __shared__ C buf[L * TC];
   const long off = (long)blockIdx.y * L * s + (long)blockIdx.x * TC;
   const int b = threadIdx.x % TC, j = threadIdx.x / TC;
@@ -472,6 +476,7 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
   }
   __syncthreads();
   const T sc = (T)1 / (T)L;
+  const T jf = (T)j;
   if (j < Q1) {
     // forward stage B: positions j + r*R0, twiddle W_L^{r j}
 #pragma unroll
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
     // v[r] is frequency j + r*R0: conj(i k~ z / L) = (-k z.y, -k z.x) with k = k~ / L
 #pragma unroll
     for (int r = 0; r < R1; ++r) {
-      T k = (T)kmask_l(j + r * R0, L) * sc;
+      T k = kmask_f<T, L>(jf + (T)(r * R0)) * sc;
       v[r] = mk<C>(-k * v[r].y, -k * v[r].x);
     }
     // inverse stage A' (radix R1) on the same values: inputs j + r*R0 = j + r*(L/R1)
@@ -539,7 +544,7 @@ __device__ __forceinline__ void tile_prefetch(cx<T>* dst, const cx<T>* in, long 
 template <typename T, int L, int TC, int R0, int R1>
 __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv2p(const cx<T>* in, cx<T>* out,
                                                                                      const cx<T>* add, long s,
-                                                                                     long ntx, long ntiles,
+                                                                                     int ntx, int ntiles,
                                                                                      const cx<T>* __restrict__ tw) {
   using C = cx<T>;
   constexpr int Q0 = L / R0;
@@ -549,16 +554,20 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
   C* bufs = reinterpret_cast<C*>(smem_raw);  // two tiles of L*TC
   const int b = threadIdx.x % TC, j = threadIdx.x / TC;
   const T sc = (T)1 / (T)L;
+  const T jf = (T)j;
   C v[R0 > R1 ? R0 : R1];
-  long t = blockIdx.x;
-  if (t < ntiles) tile_prefetch<T, L, TC, NT>(bufs, in, (t / ntx) * L * s + (t % ntx) * TC, s);
+  // tile t covers columns (t % ntx)*TC.. of pencil block t / ntx (32-bit division: the 64-bit
+  // routine runs partly on the narrow FP64 pipe)
+  auto tile_off = [&](int tt) { return (long)(tt / ntx) * L * s + (long)(tt % ntx) * TC; };
+  int t = blockIdx.x;
+  if (t < ntiles) tile_prefetch<T, L, TC, NT>(bufs, in, tile_off(t), s);
   cp_async_commit();
   for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
     C* cur = bufs + (it & 1) * L * TC;
     C* nxt = bufs + ((it + 1) & 1) * L * TC;
-    const long off = (t / ntx) * L * s + (t % ntx) * TC;
-    const long tn = t + gridDim.x;
-    if (tn < ntiles) tile_prefetch<T, L, TC, NT>(nxt, in, (tn / ntx) * L * s + (tn % ntx) * TC, s);
+    const long off = tile_off(t);
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) tile_prefetch<T, L, TC, NT>(nxt, in, tile_off(tn), s);
     cp_async_commit();
     cp_async_wait_prev();  // this tile's copies have landed (the newest group may still fly)
     __syncthreads();
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
       Dft<T, R1>::run(v);
 #pragma unroll
       for (int r = 0; r < R1; ++r) {
-        T k = (T)kmask_l(j + r * R0, L) * sc;
+        T k = kmask_f<T, L>(jf + (T)(r * R0)) * sc;
         v[r] = mk<C>(-k * v[r].y, -k * v[r].x);
       }
       Dft<T, R1>::run(v);

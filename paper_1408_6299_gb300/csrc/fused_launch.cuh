@@ -105,7 +105,7 @@ void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long o
       resident = (per_sm < 1 ? 1 : per_sm) * sms;
     }
     long grid = ntiles < resident ? ntiles : resident;
-    k_cols_deriv2p<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(in, out, add, s, ntx, ntiles, tw);
+    k_cols_deriv2p<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(in, out, add, s, (int)ntx, (int)ntiles, tw);
   } else {
     dim3 grid((unsigned)(s / TC), (unsigned)outer);
     k_cols_deriv2<T, L, TC, R0, R1><<<grid, NT, 0, st>>>(in, out, add, s, tw);

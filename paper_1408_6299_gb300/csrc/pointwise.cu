@@ -397,14 +397,15 @@ __global__ void k_seg_reduce(const double* __restrict__ a, const double* __restr
                              int nb, double* __restrict__ part) {
   __shared__ double sh[kRedThreads];
   const int p = blockIdx.y;
-  const long tot = (long)K * N1;
   double acc = 0.0;
-  for (long i = (long)blockIdx.x * kRedThreads + threadIdx.x; i < tot; i += (long)nb * kRedThreads) {
-    const long idx = ((i / N1) * B + p) * N1 + i % N1;
-    const double u = a[idx];
-    if (OP == RED_DOT) acc += u * b[idx];
-    else if (OP == RED_SQDIFF) { double t = u - b[idx]; acc += t * t; }
-    else acc = fmax(acc, fabs(u));
+  for (int k = 0; k < K; ++k) {
+    const long base = ((long)k * B + p) * N1;
+    for (long x = (long)blockIdx.x * kRedThreads + threadIdx.x; x < N1; x += (long)nb * kRedThreads) {
+      const double u = a[base + x];
+      if (OP == RED_DOT) acc += u * b[base + x];
+      else if (OP == RED_SQDIFF) { double t = u - b[base + x]; acc += t * t; }
+      else acc = fmax(acc, fabs(u));
+    }
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -426,11 +427,14 @@ __global__ void k_seg_final(const double* __restrict__ part, int nb, int B, int 
 
 // y = a_p x + c_p y per problem p (a zero coefficient drops its term, so a
 // masked problem's values never enter, whatever they hold)
+// grid: (ceil(N1 / blockDim), K * B); slice blockIdx.y is component / problem (k, p)
 __global__ void k_axpby_seg(const double* __restrict__ a, const double* __restrict__ x,
-                            const double* __restrict__ c, const double* y, double* out, int B, long N1, long n) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int p = (int)((i / N1) % B);
+                            const double* __restrict__ c, const double* y, double* out, int B, long N1, int y0) {
+  const long xi = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (xi >= N1) return;
+  const int slice = blockIdx.y + y0;
+  const int p = slice % B;
+  const long i = (long)slice * N1 + xi;
   const double ap = a[p], cp = c[p];
   out[i] = (ap != 0.0 ? ap * x[i] : 0.0) + (cp != 0.0 ? cp * y[i] : 0.0);
 }
@@ -439,8 +443,8 @@ long seg_scratch_doubles(int B) { return (long)B * 32 + B; }
 
 void seg_reduce(int op, const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
                 double* out_host) {
-  const long tot = (long)K * N1;
-  int nb = (int)((tot + 8L * kRedThreads - 1) / (8L * kRedThreads));
+  if (B > 65535) throw StatusError{1, "more than 65535 stacked problems"};
+  int nb = (int)(((long)K * N1 + 8L * kRedThreads - 1) / (8L * kRedThreads));
   nb = nb < 1 ? 1 : (nb > 32 ? 32 : nb);
   dim3 grid((unsigned)nb, (unsigned)B);
   switch (op) {
@@ -468,9 +472,12 @@ void seg_maxabs(const double* a, int K, int B, long N1, double* scratch, cudaStr
 }
 void lincomb_seg(const double* a_dev, const double* x, const double* c_dev, const double* y, double* out, int K,
                  int B, long N1, cudaStream_t s) {
-  const long n = (long)K * B * N1;
-  k_axpby_seg<<<nblk(n), 256, 0, s>>>(a_dev, x, c_dev, y, out, B, N1, n);
-  REG_LAUNCH();
+  for (int y0 = 0; y0 < K * B; y0 += 65535) {  // grid.y is limited to 65535 slices per launch
+    const int ny = K * B - y0 < 65535 ? K * B - y0 : 65535;
+    dim3 grid(nblk(N1), (unsigned)ny);
+    k_axpby_seg<<<grid, 256, 0, s>>>(a_dev, x, c_dev, y, out, B, N1, y0);
+    REG_LAUNCH();
+  }
 }
 
 // result (device, 4 doubles at scratch + 4*kRedBlocks): {sum, sumsq, min, max}
