@@ -51,7 +51,11 @@ template <typename T, int L, int NF, int EPI>
 void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
            const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc) {
   constexpr int M = L / 2;
-  constexpr int RB0 = row_elems<T>() / (pow2_ceil(NF) * M);
+  // single precision: 512 complex values per field and block for one field,
+  // 1024 for more (4 and 8 rows at L = 256), so that the epilogue operand
+  // slices stay within the prefetch limit (measured on the 256^3 matvec:
+  // 298 -> 290 ms against the element-count rule of the other passes)
+  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NF == 1 ? 8 : 4) * M) : row_elems<T>() / (pow2_ceil(NF) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
   ProfScope ps(KK_ROWS_C2R, s, bytes);
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
