@@ -276,8 +276,15 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
                   (e.out1 ? d + (e.src ? 1 : (e.gm[0] ? 2 * d : 0)) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1) : 0));
   DivEpi<T> none{};
   if (d == 3) {
+    // the two strided passes are independent: the x pass runs on the second
+    // stream, so each fills the other's last partial wave of blocks
+    cudaStream_t s2 = sp.aux_stream();
+    REG_CUDA(cudaEventRecord(sp.fork_event(), s));
+    REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
+    deriv<T>(g, sp, 0, U, Zx, nullptr, s2);
     deriv<T>(g, sp, 1, U, Zy, nullptr, s);
-    deriv<T>(g, sp, 0, U, Zx, nullptr, s);
+    REG_CUDA(cudaEventRecord(sp.join_event(), s2));
+    REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
     RowsSpec<T, 3> in{{Zx, Zy, U}};
     c2r<T, 3, EPI_ADV>(g, s, in, 1 << 2, e, none, bytes, tw, twrc);
   } else {

@@ -139,10 +139,18 @@ class Spectral {
   const C* twiddles(int L) const;   // Stockham stage tables for length L
   const C* rc_twiddles() const;     // exp(-2 pi i k / L_last), k < M
 
+  // A second stream with a fork and a join event, for independent passes of
+  // one stage (created on first use).
+  cudaStream_t aux_stream();
+  cudaEvent_t fork_event() const { return ev_fork_; }
+  cudaEvent_t join_event() const { return ev_join_; }
+
  private:
   void cols(C* U, int axis, bool inverse);
   Grid g_;
   cudaStream_t s_;
+  cudaStream_t aux_ = nullptr;
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   C* tw_ = nullptr;  // device: tables per length + real/complex table
   bool owns_ = true;
   long tw_off_[11] = {0};  // offset of the table of length 2^e

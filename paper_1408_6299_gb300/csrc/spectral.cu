@@ -551,6 +551,19 @@ long Spectral<T>::write_tables(double* out, long* tw_off, long* rc_off) {
 template <typename T>
 Spectral<T>::~Spectral() {
   if (tw_ && owns_) cudaFree(tw_);
+  if (ev_fork_) cudaEventDestroy(ev_fork_);
+  if (ev_join_) cudaEventDestroy(ev_join_);
+  if (aux_) cudaStreamDestroy(aux_);
+}
+
+template <typename T>
+cudaStream_t Spectral<T>::aux_stream() {
+  if (!aux_) {
+    REG_CUDA(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+    REG_CUDA(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
+    REG_CUDA(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+  }
+  return aux_;
 }
 
 template <typename T>
