@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--cfl", type=float, default=0.2)
     p.add_argument("--as-configured-steps", type=int, default=2)
     p.add_argument("--store-all-steps", type=int, default=2)
+    p.add_argument("--newton-steps", type=int, default=2)
     p.add_argument("--ckpt", type=int, default=8)
     p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -467,6 +468,26 @@ def run_ours(args):
         Rs.close()
         torch.cuda.empty_cache()
 
+    # the full Newton matvec (N-PCG) in the headline configuration
+    newton = None
+    if args.newton_steps > 0:
+        Rn = lib.Registration(c["n"], n_t, c["n_c"], c["beta"], c["reg"], c["stokes"], lib.REG_MIXED, args.ckpt,
+                              hessian=lib.REG_HESS_NEWTON)
+        Rn.set_images(mT, mR)
+        Rn.linearize(v)
+        Hn = torch.empty_like(g)
+        Rn.hessvec(vt, Hn)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.newton_steps):
+            Rn.hessvec(vt, Hn)
+        torch.cuda.synchronize()
+        tn = (time.perf_counter() - t0) / args.newton_steps
+        newton = {"value": 1.0 / tn, "unit": UNIT, "ckpt_every": args.ckpt,
+                  "note": "same point as the headline (m_R = m_1 there, so the result equals Gauss-Newton)"}
+        Rn.close()
+        torch.cuda.empty_cache()
+
     # the workload's own n_t (unstable at the top modes in single precision)
     as_cfg = None
     if args.as_configured_steps > 0 and n_t != nt_cfg:
@@ -518,7 +539,7 @@ def run_ours(args):
                        "precision": "mixed (f32 sweeps, f64 force/tail/vectors)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "clocks": ck, "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "fp64": fp64,
-            "store_all": store_all, "as_configured": as_cfg, "solve_to_rel_grad_1e-2": solves, "batch_2d": batch, "cpu_baseline": cpu,
+            "store_all": store_all, "newton": newton, "as_configured": as_cfg, "solve_to_rel_grad_1e-2": solves, "batch_2d": batch, "cpu_baseline": cpu,
             "kernel_ms_per_matvec": {k: round(v["ms"], 3) for k, v in prof_all.items()},
         }
         print(json.dumps(line), flush=True)
