@@ -15,6 +15,8 @@
 // so a 3D stage costs four passes over the field and no separate pointwise
 // kernel, and the gradient fields are never written unless they are kept.
 #pragma once
+#include <cuda.h>
+
 #include "internal.h"
 
 namespace reg {
@@ -620,6 +622,152 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
   }
   cp_async_wait_prev();
   asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// TMA form of k_cols_deriv2p: one thread brings each tile (TC columns x L
+// rows of the strided pencils) into shared memory with a 2D tensor copy
+// (cp.async.bulk.tensor) that completes on an mbarrier; the other threads
+// issue no copy instructions. Every wait is bounded: a block whose copy does
+// not land within the bound counts a timeout in g_tma_timeouts (read by the
+// host) and stops.
+// ---------------------------------------------------------------------------
+static __device__ int g_tma_timeouts;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// wait for the phase with parity `parity`; false when the bound runs out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 20); ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// The tensor map views the input as rows of s complex values (4-byte
+// elements, s * sizeof(cx<T>) / 4 per row) and outer * L rows; tile t is the
+// box at x = (t % ntx) * TC complex values, y = (t / ntx) * L rows.
+template <typename T, int L, int TC, int R0, int R1>
+__global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv2t(const __grid_constant__ CUtensorMap tmap,
+                                                                                     cx<T>* out, const cx<T>* add, long s,
+                                                                                     int ntx, int ntiles,
+                                                                                     const cx<T>* __restrict__ tw) {
+  using C = cx<T>;
+  constexpr int Q0 = L / R0;
+  constexpr int Q1 = R0;
+  constexpr unsigned TILE_BYTES = L * TC * sizeof(C);
+  constexpr int XW = TC * (int)sizeof(C) / 4;  // box width in 4-byte elements
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  C* bufs = reinterpret_cast<C*>(smem_raw);  // two tiles of L*TC
+  const int b = threadIdx.x % TC, j = threadIdx.x / TC;
+  const T sc = (T)1 / (T)L;
+  const T jf = (T)j;
+  C v[R0 > R1 ? R0 : R1];
+  auto tile_off = [&](int tt) { return (long)(tt / ntx) * L * s + (long)(tt % ntx) * TC; };
+  auto issue = [&](int tt, int buf) {  // one thread
+    mbar_expect_tx(&bar[buf], TILE_BYTES);
+    tma_load_2d(bufs + buf * L * TC, &tmap, (tt % ntx) * XW, (tt / ntx) * L, &bar[buf]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  int t = blockIdx.x;
+  if (threadIdx.x == 0 && t < ntiles) issue(t, 0);
+  int it = 0;
+  bool pending_other = false;  // a copy into the other buffer is in flight
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int cb = it & 1;
+    C* cur = bufs + cb * L * TC;
+    const long off = tile_off(t);
+    const int tn = t + gridDim.x;
+    pending_other = tn < ntiles;
+    if (threadIdx.x == 0 && pending_other) issue(tn, cb ^ 1);
+    // all threads agree on the outcome, so a timeout ends the whole block together
+    if (!__syncthreads_and(mbar_wait(&bar[cb], (it >> 1) & 1))) {
+      if (threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1);
+      break;
+    }
+    // forward stage A from the staged tile
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[r] = cur[(j + r * Q0) * TC + b];
+      Dft<T, R0>::run(v);
+    }
+    __syncthreads();
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) cur[(j * R0 + r) * TC + b] = v[r];
+    }
+    __syncthreads();
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) v[r] = cur[(j + r * R0) * TC + b];
+#pragma unroll
+      for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], __ldg(&tw[r * R0 + j]));
+      Dft<T, R1>::run(v);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        T k = kmask_f<T, L>(jf + (T)(r * R0)) * sc;
+        v[r] = mk<C>(-k * v[r].y, -k * v[r].x);
+      }
+      Dft<T, R1>::run(v);
+    }
+    __syncthreads();
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) cur[(j * R1 + r) * TC + b] = v[r];
+    }
+    __syncthreads();
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[r] = cur[(j + r * Q0) * TC + b];
+#pragma unroll
+      for (int r = 1; r < R0; ++r) v[r] = cmul(v[r], __ldg(&tw[j * R0 + r]));
+      Dft<T, R0>::run(v);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        C z = cconj(v[r]);
+        long o = off + (long)(j + r * Q0) * s + b;
+        if (add) z = cadd(z, add[o]);
+        out[o] = z;
+      }
+    }
+    // the shared-memory writes above precede, in the async proxy, the tensor
+    // copy that refills this buffer in the next iteration
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    pending_other = false;
+  }
+  // after a timeout the copies issued for this and the next tile may still be
+  // in flight: wait for them (bounded) before the block's shared memory is released
+  if (t < ntiles) {
+    (void)mbar_wait(&bar[it & 1], (it >> 1) & 1);
+    if (pending_other) (void)mbar_wait(&bar[(it & 1) ^ 1], ((it + 1) >> 1) & 1);
+  }
 }
 
 }  // namespace fused

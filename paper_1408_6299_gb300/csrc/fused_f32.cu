@@ -12,4 +12,17 @@ void div_stage<float>(Spectral<float>& sp, const float* lam, const float* a, con
                       float2* Q0, float2* Q1, float2* Q2) {
   fused::div_stage_impl<float>(sp, lam, a, e, Q0, Q1, Q2);
 }
+
+// timeouts of the TMA column pass of this precision since the last call (reset on read)
+int take_tma_timeouts_f32(cudaStream_t s) {
+  int h = 0;
+  REG_CUDA(cudaMemcpyFromSymbolAsync(&h, fused::g_tma_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  REG_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    const int z = 0;
+    REG_CUDA(cudaMemcpyToSymbolAsync(fused::g_tma_timeouts, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    REG_CUDA(cudaStreamSynchronize(s));
+  }
+  return h;
+}
 }  // namespace reg

@@ -12,4 +12,17 @@ void div_stage<double>(Spectral<double>& sp, const double* lam, const double* a,
                        double2* Q0, double2* Q1, double2* Q2) {
   fused::div_stage_impl<double>(sp, lam, a, e, Q0, Q1, Q2);
 }
+
+// timeouts of the TMA column pass of this precision since the last call (reset on read)
+int take_tma_timeouts_f64(cudaStream_t s) {
+  int h = 0;
+  REG_CUDA(cudaMemcpyFromSymbolAsync(&h, fused::g_tma_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  REG_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    const int z = 0;
+    REG_CUDA(cudaMemcpyToSymbolAsync(fused::g_tma_timeouts, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    REG_CUDA(cudaStreamSynchronize(s));
+  }
+  return h;
+}
 }  // namespace reg

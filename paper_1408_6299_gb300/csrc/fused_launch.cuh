@@ -89,7 +89,46 @@ void deriv_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long ou
   REG_LAUNCH();
 }
 
-// variant 0: persistent double-buffered, tile width TCmax; variants 1..3:
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+inline EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of the strided pencils of one column pass (rows of s complex
+// values as 4-byte elements, outer * L rows; box TC complex x L rows). False
+// when the shape is not expressible (L > 256 rows per box) or the encoder
+// refuses it.
+template <typename T, int L, int TC>
+bool cols_tensor_map(CUtensorMap* m, const cx<T>* in, long s, long outer) {
+  if (L > 256) return false;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)s * sizeof(cx<T>) / 4, (cuuint64_t)outer * L};
+  cuuint64_t strides[1] = {(cuuint64_t)s * sizeof(cx<T>)};
+  cuuint32_t box[2] = {(cuuint32_t)(TC * sizeof(cx<T>) / 4), (cuuint32_t)L};
+  cuuint32_t es[2] = {1, 1};
+  if (((uintptr_t)in & 15) || (strides[0] & 15) || box[0] > 256) return false;
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<cx<T>*>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// variant 0: persistent double-buffered, tile width TCmax (tiles by TMA where
+// a tensor map can describe them, else by cp.async); variants 1..3:
 // one block per tile with widths TCmax, TCmax/2, 4
 template <typename T, int L, int TC, bool PERSIST>
 void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
@@ -100,6 +139,23 @@ void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long o
   const long ntx = s / TC, ntiles = ntx * outer;
   if constexpr (PERSIST) {
     constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
+    CUtensorMap map;
+    if (cols_tensor_map<T, L, TC>(&map, in, s, outer)) {
+      static int resident_t = 0;
+      if (resident_t == 0) {
+        auto kern = k_cols_deriv2t<T, L, TC, R0, R1>;
+        REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0, dev = 0, sms = 0;
+        REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+        REG_CUDA(cudaGetDevice(&dev));
+        REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        resident_t = (per_sm < 1 ? 1 : per_sm) * sms;
+      }
+      long grid = ntiles < resident_t ? ntiles : resident_t;
+      k_cols_deriv2t<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(map, out, add, s, (int)ntx, (int)ntiles, tw);
+      REG_LAUNCH();
+      return;
+    }
     static int resident = 0;
     if (resident == 0) {
       auto kern = k_cols_deriv2p<T, L, TC, R0, R1>;

@@ -161,6 +161,11 @@ class Spectral {
 // Fused Heun stages (fused.cuh): advection k = -v.grad u [- grad m . v~] and
 // divergence k = div(v lam), each with its Runge-Kutta update in the last pass.
 // ---------------------------------------------------------------------------
+// bounded waits of the TMA column pass that gave up since the last call
+// (per precision; synchronises s)
+int take_tma_timeouts_f32(cudaStream_t s);
+int take_tma_timeouts_f64(cudaStream_t s);
+
 namespace fused {
 template <typename T>
 struct AdvEpi;

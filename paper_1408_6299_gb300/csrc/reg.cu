@@ -1663,6 +1663,12 @@ void reg::set_thread_error(const std::string& msg) { g_create_error = msg; }
 
 namespace {
 
+// a tile copy of the TMA column pass that never landed leaves garbage: fail the call
+void check_copies(reg_ctx* c) {
+  if (take_tma_timeouts_f32(c->s) + take_tma_timeouts_f64(c->s) > 0)
+    throw StatusError{REG_ETIMEOUT, "a tile copy of the column pass timed out"};
+}
+
 reg_status fail(reg_ctx* c, int st, const std::string& msg) {
   if (c) c->err = msg;
   else g_create_error = msg;
@@ -1678,6 +1684,7 @@ reg_status fail(reg_ctx* c, int st, const std::string& msg) {
   tl_prof = c_->prof.mask ? &c_->prof : nullptr;                \
   try {
 #define API_END                                                                                       \
+  check_copies(c_);                                                                                   \
   }                                                                                                   \
   catch (const StatusError& e) {                                                                      \
     return fail(c_, e.status, e.what);                                                                \
