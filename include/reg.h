@@ -410,6 +410,14 @@ REG_API reg_status reg_profile_end(reg_ctx* ctx, double* ms, double* bytes, long
 /* Number of kernel launches issued by the library in this process so far. */
 REG_API long reg_launch_count(void);
 
+/* Failure-path check of the bounded waits (no counterpart in the paper): one
+ * block polls an mbarrier that nothing completes, gives up after a bounded
+ * number of polls, and counts the timeout the way the TMA column pass counts
+ * a tile copy that never lands (which fails the API call with
+ * REG_ETIMEOUT). *counted: the timeouts read back and cleared (1 expected).
+ * Faults, traps and hangs nothing; uses the current device. */
+REG_API reg_status reg_selftest_copy_timeout(int* counted);
+
 #ifdef __cplusplus
 }
 #endif

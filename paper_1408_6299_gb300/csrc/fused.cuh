@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
   constexpr int Q0 = L / R0;
   constexpr int Q1 = R0;
   constexpr int NT = TC * (Q0 > Q1 ? Q0 : Q1);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* bufs = reinterpret_cast<C*>(smem_raw);  // two tiles of L*TC
   const int b = threadIdx.x % TC, j = threadIdx.x / TC;
   const T sc = (T)1 / (T)L;
@@ -644,8 +644,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 // wait for the phase with parity `parity`; false when the bound runs out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 20); ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int tries = 1 << 20) {
+  for (int i = 0; i < tries; ++i) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -662,6 +662,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
           "r"(smem_addr(dst)),
       "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
       : "memory");
+}
+
+// Failure-path check: one block waits on an mbarrier that nothing completes,
+// gives up after `tries` polls and counts the timeout as the column pass does.
+static __global__ void k_wait_timeout_probe(int tries) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (!__syncthreads_and(mbar_wait(&bar, 0, tries)) && threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1);
 }
 
 // The tensor map views the input as rows of s complex values (4-byte

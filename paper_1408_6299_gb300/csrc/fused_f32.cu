@@ -1,4 +1,5 @@
 // fused_f32.cu -- single precision instantiation of the fused transport stages.
+#include "../../include/reg.h"
 #include "fused_launch.cuh"
 
 namespace reg {
@@ -26,3 +27,17 @@ int take_tma_timeouts_f32(cudaStream_t s) {
   return h;
 }
 }  // namespace reg
+
+extern "C" reg_status reg_selftest_copy_timeout(int* counted) {
+  if (!counted) return REG_EINVAL;
+  try {
+    reg::fused::k_wait_timeout_probe<<<1, 32>>>(1 << 12);
+    REG_CUDA(cudaGetLastError());
+    REG_CUDA(cudaDeviceSynchronize());
+    *counted = reg::take_tma_timeouts_f32(nullptr);
+  } catch (const reg::CudaError& e) {
+    reg::set_thread_error(e.what);
+    return REG_ECUDA;
+  }
+  return REG_OK;
+}

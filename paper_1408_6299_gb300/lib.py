@@ -176,6 +176,7 @@ _SIGNATURES = {
     "reg_smooth": [_vp, ctypes.c_double, _vp, _vp],
     "reg_lanczos": [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int), _vp],
     "reg_set_beta": [_vp, ctypes.c_double],
+    "reg_selftest_copy_timeout": [ctypes.POINTER(ctypes.c_int)],
     "reg_set_time_steps": [_vp, ctypes.c_int],
     "reg_continuation": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(ContOpts), ctypes.POINTER(ContReport)],
     "reg_solve": [_vp, _vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
@@ -192,6 +193,16 @@ _SIGNATURES = {
 EXPORTED = tuple(_SIGNATURES) + ("reg_last_error", "reg_solve_opts_default", "reg_launch_count",
                                   "reg_cont_opts_default")
 KIND_NAMES = ("rows_r2c", "rows_c2r", "cols", "mult", "stage", "force", "other")
+
+
+def selftest_copy_timeout():
+    """Number of timeouts counted by the bounded-wait self-test (1 expected)."""
+    L = load()
+    n = ctypes.c_int(0)
+    st = L.reg_selftest_copy_timeout(ctypes.byref(n))
+    if st != REG_OK:
+        raise RegError(st, L.reg_last_error(None).decode())
+    return n.value
 
 
 def launch_count():
