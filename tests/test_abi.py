@@ -69,3 +69,16 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_solve_option_defaults_and_unknown_names():
+    L = lib.load()
+    o = lib.SolveOpts.make(L, {"grad_rtol": 1e-3, "method": lib.REG_METHOD_PICARD})
+    assert o.grad_rtol == 1e-3 and o.method == lib.REG_METHOD_PICARD
+    assert o.max_outer == 50 and o.step_memory == 1 and o.stop_rule == lib.REG_STOP_GRAD_REL and o.tau_J == 1e-3
+    import pytest
+    with pytest.raises(TypeError):
+        lib.SolveOpts.make(L, {"grad_rtoll": 1e-3})
+    c = lib.ContOpts()
+    L.reg_cont_opts_default(ctypes.byref(c))
+    assert (c.beta0, c.beta_min, c.eps_F, c.beta_rtol, c.dist_rtol, c.max_solves) == (1.0, 1e-6, 0.1, 0.05, 1e-2, 50)
