@@ -192,3 +192,27 @@ def test_bad_arguments_are_rejected():
         lib.Registration((16, 16), 6, ckpt_every=4)
     with pytest.raises(lib.RegError):
         lib.Registration((16, 16), 4, beta=-1.0)
+
+
+@pytest.mark.parametrize("n", [(512, 512), (512, 8), (8, 512), (8, 16, 512), (512, 8, 8)],
+                         ids=["512x512", "512x8", "8x512", "8x16x512", "512x8x8"])
+def test_extreme_grid_shapes(n):
+    # the largest and smallest admissible axis lengths (8 and 512) on rows and on strided axes; the
+    # speed keeps the CFL number below 0.2 with n_t = 2 on the 512-point axis (Heun is unstable above 1)
+    r = np.random.default_rng(91)
+    mT = synth.random_spectral_field(n, r, 3.0)
+    v = np.stack([synth.velocity_field(n, r, 2, 0.004)])
+    vt = np.stack([synth.velocity_field(n, r, 2, 1.0)])
+    c = dict(n=n, n_t=2, n_c=1, beta=1e-2, reg=1, stokes=False)
+    P = O.Problem(n, 2, 1, 1e-2, 1, False)
+    mR = P.state(v, mT)[-1]
+    for precision, tol in ((lib.REG_FP64, FP64_TOL), (lib.REG_MIXED, MIXED_TOL)):
+        R, _ = pair(c, precision=precision)
+        R.set_images(cuda(mT), cuda(mR))
+        g = empty(R.coef_shape())
+        R.gradient(cuda(0.5 * v), g)
+        go, _ = P.gradient(0.5 * v, mT, mR)
+        assert rel(host(g), go) < FP64_TOL, (n, precision)  # the gradient is FP64 in both precisions
+        Hv = empty(R.coef_shape())
+        R.hessvec(cuda(vt), Hv)
+        assert rel(host(Hv), P.hessvec(0.5 * v, mT, vt)) < tol, (n, precision)
