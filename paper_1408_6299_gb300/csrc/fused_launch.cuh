@@ -127,6 +127,18 @@ bool cols_tensor_map(CUtensorMap* m, const cx<T>* in, long s, long outer) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// blocks of kernel `kern` (nt threads, smem dynamic bytes) resident on the
+// whole current device at once
+template <typename K>
+int persistent_wave(K kern, int nt, size_t smem) {
+  REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, dev = 0, sms = 0;
+  REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+  REG_CUDA(cudaGetDevice(&dev));
+  REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return (per_sm < 1 ? 1 : per_sm) * sms;
+}
+
 // variant 0: persistent double-buffered, tile width TCmax (tiles by TMA where
 // a tensor map can describe them, else by cp.async); variants 1..3:
 // one block per tile with widths TCmax, TCmax/2, 4
@@ -141,31 +153,15 @@ void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long o
     constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
     CUtensorMap map;
     if (cols_tensor_map<T, L, TC>(&map, in, s, outer)) {
-      static int resident_t = 0;
-      if (resident_t == 0) {
-        auto kern = k_cols_deriv2t<T, L, TC, R0, R1>;
-        REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0, dev = 0, sms = 0;
-        REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-        REG_CUDA(cudaGetDevice(&dev));
-        REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        resident_t = (per_sm < 1 ? 1 : per_sm) * sms;
-      }
+      // resident blocks of one wave, computed once per instantiation (thread-safe static initialisation;
+      // retried on the next call if a query throws)
+      static const int resident_t = persistent_wave(k_cols_deriv2t<T, L, TC, R0, R1>, NT, smem);
       long grid = ntiles < resident_t ? ntiles : resident_t;
       k_cols_deriv2t<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(map, out, add, s, (int)ntx, (int)ntiles, tw);
       REG_LAUNCH();
       return;
     }
-    static int resident = 0;
-    if (resident == 0) {
-      auto kern = k_cols_deriv2p<T, L, TC, R0, R1>;
-      REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int per_sm = 0, dev = 0, sms = 0;
-      REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-      REG_CUDA(cudaGetDevice(&dev));
-      REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      resident = (per_sm < 1 ? 1 : per_sm) * sms;
-    }
+    static const int resident = persistent_wave(k_cols_deriv2p<T, L, TC, R0, R1>, NT, smem);
     long grid = ntiles < resident ? ntiles : resident;
     k_cols_deriv2p<T, L, TC, R0, R1><<<(unsigned)grid, NT, smem, st>>>(in, out, add, s, (int)ntx, (int)ntiles, tw);
   } else {
