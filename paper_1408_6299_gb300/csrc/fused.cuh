@@ -125,6 +125,7 @@ struct AdvEpi {
   T* Sout;
   T h;
   int stage;
+  int src_from_a;  // two-field stage, second field: the source is the first field's Sout value
 };
 
 // Epilogue parameters of the divergence stage (adjoint / incremental adjoint).
@@ -159,7 +160,7 @@ struct RowsSpec {
   const cx<T>* p[NF];
 };
 
-enum { EPI_ADV = 1, EPI_DIV = 2 };
+enum { EPI_ADV = 1, EPI_DIV = 2, EPI_ADV2 = 3 };  // ADV2: two advection epilogues on 2 x d fields
 
 // Hint: fetch a contiguous byte range into L2 (bulk prefetch; no completion to wait for).
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -172,9 +173,9 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
 // operand each; only operands the epilogue will read are requested.
 template <typename T, int NF, int EPI>
 __device__ __forceinline__ void prefetch_epilogue(const AdvEpi<T>& adv, const DivEpi<T>& dv, long off,
-                                                  unsigned bytes) {
-  const int k = threadIdx.x;
-  if (k >= 64) return;
+                                                  unsigned bytes, int first_thread = 0) {
+  const int k = (int)threadIdx.x - first_thread;
+  if (k < 0 || k >= 64) return;
   const T* p = nullptr;
   if (EPI == EPI_ADV) {
     if (adv.out1) {
@@ -203,13 +204,70 @@ __device__ __forceinline__ void prefetch_epilogue(const AdvEpi<T>& adv, const Di
   if (p && ((reinterpret_cast<unsigned long long>(p + off) | bytes) & 15) == 0) l2_prefetch(p + off, bytes);
 }
 
+// Advection epilogue on the point pair q with the gradient components g[0..D)
+// (-a.g [- source], Heun update, optional keep of g or of g.sw). srcv, when
+// given, is the source value instead of e.src. Returns the Sout value.
+template <typename T, int D>
+__device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, long q, const cx<T>* srcv) {
+  using C = cx<T>;
+  C so = mk<C>(0, 0);
+  if (e.G[0]) {
+#pragma unroll
+    for (int f = 0; f < D; ++f) reinterpret_cast<C*>(e.G[f])[q] = g[f];
+  }
+  if (e.Sout) {
+    T s0 = 0, s1 = 0;
+#pragma unroll
+    for (int f = 0; f < D; ++f) {
+      C w = reinterpret_cast<const C*>(e.sw[f])[q];
+      s0 += g[f].x * w.x;
+      s1 += g[f].y * w.y;
+    }
+    so = mk<C>(s0, s1);
+    reinterpret_cast<C*>(e.Sout)[q] = so;
+  }
+  if (!e.out1) return so;
+  T k0 = 0, k1 = 0;
+#pragma unroll
+  for (int f = 0; f < D; ++f) {
+    C a = reinterpret_cast<const C*>(e.a[f])[q];
+    k0 -= a.x * g[f].x;
+    k1 -= a.y * g[f].y;
+  }
+  if (srcv) {
+    k0 -= srcv->x;
+    k1 -= srcv->y;
+  } else if (e.src) {
+    C sv = reinterpret_cast<const C*>(e.src)[q];
+    k0 -= sv.x;
+    k1 -= sv.y;
+  } else if (e.gm[0]) {
+#pragma unroll
+    for (int f = 0; f < D; ++f) {
+      C gm = reinterpret_cast<const C*>(e.gm[f])[q];
+      C w = reinterpret_cast<const C*>(e.w[f])[q];
+      k0 -= gm.x * w.x;
+      k1 -= gm.y * w.y;
+    }
+  }
+  if (e.stage == 1) {
+    C yv = e.y ? reinterpret_cast<const C*>(e.y)[q] : mk<C>(0, 0);
+    reinterpret_cast<C*>(e.out1)[q] = mk<C>(yv.x + e.h * k0, yv.y + e.h * k1);
+    reinterpret_cast<C*>(e.out2)[q] = mk<C>(yv.x + (T)0.5 * e.h * k0, yv.y + (T)0.5 * e.h * k1);
+  } else {
+    C yv = reinterpret_cast<const C*>(e.y)[q];
+    reinterpret_cast<C*>(e.out1)[q] = mk<C>(yv.x + (T)0.5 * e.h * k0, yv.y + (T)0.5 * e.h * k1);
+  }
+  return so;
+}
+
 // Inverse row transforms of one staged row block (NF fields x RB rows of
 // packed spectra in buf, padded rows of RS) and the stage epilogue of rows
 // row0..row0+RB-1. Called by all threads of the block after buf is complete.
 template <typename T, int L, int RB, int NF, int EPI>
 __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
                                           const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
-                                          const cx<T>* __restrict__ twrc) {
+                                          const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB) {
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
@@ -245,49 +303,10 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
       g[f] = mk<C>(z.x * s, -z.y * s);
     }
     if (EPI == EPI_ADV) {
-      if (adv.G[0]) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) reinterpret_cast<C*>(adv.G[f])[q] = g[f];
-      }
-      if (adv.Sout) {
-        T s0 = 0, s1 = 0;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          C w = reinterpret_cast<const C*>(adv.sw[f])[q];
-          s0 += g[f].x * w.x;
-          s1 += g[f].y * w.y;
-        }
-        reinterpret_cast<C*>(adv.Sout)[q] = mk<C>(s0, s1);
-      }
-      if (!adv.out1) continue;
-      T k0 = 0, k1 = 0;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        C a = reinterpret_cast<const C*>(adv.a[f])[q];
-        k0 -= a.x * g[f].x;
-        k1 -= a.y * g[f].y;
-      }
-      if (adv.src) {
-        C sv = reinterpret_cast<const C*>(adv.src)[q];
-        k0 -= sv.x;
-        k1 -= sv.y;
-      } else if (adv.gm[0]) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          C gm = reinterpret_cast<const C*>(adv.gm[f])[q];
-          C w = reinterpret_cast<const C*>(adv.w[f])[q];
-          k0 -= gm.x * w.x;
-          k1 -= gm.y * w.y;
-        }
-      }
-      if (adv.stage == 1) {
-        C yv = adv.y ? reinterpret_cast<const C*>(adv.y)[q] : mk<C>(0, 0);
-        reinterpret_cast<C*>(adv.out1)[q] = mk<C>(yv.x + adv.h * k0, yv.y + adv.h * k1);
-        reinterpret_cast<C*>(adv.out2)[q] = mk<C>(yv.x + (T)0.5 * adv.h * k0, yv.y + (T)0.5 * adv.h * k1);
-      } else {
-        C yv = reinterpret_cast<const C*>(adv.y)[q];
-        reinterpret_cast<C*>(adv.out1)[q] = mk<C>(yv.x + (T)0.5 * adv.h * k0, yv.y + (T)0.5 * adv.h * k1);
-      }
+      adv_point<T, NF>(adv, g, q, nullptr);
+    } else if (EPI == EPI_ADV2) {
+      const C sa = adv_point<T, NF / 2>(adv, g, q, nullptr);
+      adv_point<T, NF / 2>(advB, g + NF / 2, q, advB.src_from_a ? &sa : nullptr);
     } else {
       C k = g[0];
       if (dv.src) {
@@ -369,7 +388,7 @@ template <typename T, int L, int RB, int NF, int EPI>
 // 285.0 -> 280.5 ms against five; the divergence epilogue spills a few words and still gains.
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n(RowsSpec<T, NF> in, int zmask, AdvEpi<T> adv,
                                                           DivEpi<T> dv, long nrows, const cx<T>* __restrict__ tw,
-                                                          const cx<T>* __restrict__ twrc) {
+                                                          const cx<T>* __restrict__ twrc, AdvEpi<T> advB) {
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
@@ -391,7 +410,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n
   // resident blocks of the whole GPU keep in L2 (measured: re-read traffic)
   if constexpr (RB * L * sizeof(T) <= 8192) {
     const long nr = nrows - row0 < RB ? nrows - row0 : RB;
-    prefetch_epilogue<T, NF, EPI>(adv, dv, row0 * L, (unsigned)(nr * L * sizeof(T)));
+    if constexpr (EPI == EPI_ADV2) {
+      prefetch_epilogue<T, NF / 2, EPI_ADV>(adv, dv, row0 * L, (unsigned)(nr * L * sizeof(T)));
+      prefetch_epilogue<T, NF / 2, EPI_ADV>(advB, dv, row0 * L, (unsigned)(nr * L * sizeof(T)), 64);
+    } else {
+      prefetch_epilogue<T, NF, EPI>(adv, dv, row0 * L, (unsigned)(nr * L * sizeof(T)));
+    }
   }
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
@@ -405,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n
     }
   }
   __syncthreads();
-  c2r_block<T, L, RB, NF, EPI>(buf, row0, nrows, adv, dv, tw, twrc);
+  c2r_block<T, L, RB, NF, EPI>(buf, row0, nrows, adv, dv, tw, twrc, advB);
 }
 
 // Spectral derivative along a strided axis of length L on z-spectral rows:

@@ -9,6 +9,11 @@ void adv_stage<float>(Spectral<float>& sp, const float* u, const fused::AdvEpi<f
   fused::adv_stage_impl<float>(sp, u, e, U, Zx, Zy);
 }
 template <>
+void adv2_stage<float>(Spectral<float>& sp, const float* uA, const fused::AdvEpi<float>& eA, const float* uB,
+                      const fused::AdvEpi<float>& eB, float2* const* Z) {
+  fused::adv2_stage_impl<float>(sp, uA, eA, uB, eB, Z);
+}
+template <>
 void div_stage<float>(Spectral<float>& sp, const float* lam, const float* a, const fused::DivEpi<float>& e,
                       float2* Q0, float2* Q1, float2* Q2) {
   fused::div_stage_impl<float>(sp, lam, a, e, Q0, Q1, Q2);

@@ -8,6 +8,11 @@ void adv_stage<double>(Spectral<double>& sp, const double* u, const fused::AdvEp
   fused::adv_stage_impl<double>(sp, u, e, U, Zx, Zy);
 }
 template <>
+void adv2_stage<double>(Spectral<double>& sp, const double* uA, const fused::AdvEpi<double>& eA, const double* uB,
+                      const fused::AdvEpi<double>& eB, double2* const* Z) {
+  fused::adv2_stage_impl<double>(sp, uA, eA, uB, eB, Z);
+}
+template <>
 void div_stage<double>(Spectral<double>& sp, const double* lam, const double* a, const fused::DivEpi<double>& e,
                        double2* Q0, double2* Q1, double2* Q2) {
   fused::div_stage_impl<double>(sp, lam, a, e, Q0, Q1, Q2);

@@ -51,31 +51,33 @@ void r2c(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, c
 
 template <typename T, int L, int NF, int EPI>
 void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
-           const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc) {
+           const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc, const AdvEpi<T>& advB) {
   constexpr int M = L / 2;
   // single precision: 512 complex values per field and block for one field,
   // 1024 for more (4 and 8 rows at L = 256), so that the epilogue operand
   // slices stay within the prefetch limit (measured on the 256^3 matvec:
   // 298 -> 290 ms against the element-count rule of the other passes)
-  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NF == 1 ? 8 : 4) * M) : row_elems<T>() / (pow2_ceil(NF) * M);
+  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NF == 1 || NF > 4 ? 8 : 4) * M)
+                                     : row_elems<T>() / ((NF > 4 ? 8 : pow2_ceil(NF)) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
   ProfScope ps(KK_ROWS_C2R, s, bytes);
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
-  k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc);
+  k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc, advB);
   REG_LAUNCH();
 }
 
 template <typename T, int NF, int EPI>
 void c2r(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
-         const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc) {
+         const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc,
+         const AdvEpi<T>& advB = AdvEpi<T>{}) {
   switch (g.L) {
-    case 8: return c2r_L<T, 8, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 16: return c2r_L<T, 16, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 32: return c2r_L<T, 32, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 64: return c2r_L<T, 64, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 128: return c2r_L<T, 128, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 256: return c2r_L<T, 256, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
-    case 512: return c2r_L<T, 512, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc);
+    case 8: return c2r_L<T, 8, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 16: return c2r_L<T, 16, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 32: return c2r_L<T, 32, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 64: return c2r_L<T, 64, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 128: return c2r_L<T, 128, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 256: return c2r_L<T, 256, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 512: return c2r_L<T, 512, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
   }
   throw StatusError{1, "unsupported last-axis length"};
 }
@@ -344,6 +346,46 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
     RowsSpec<T, 2> in{{Zy, U}};
     c2r<T, 2, EPI_ADV>(g, s, in, 1 << 1, e, none, bytes, tw, twrc);
   }
+}
+
+// Two advection stages of 3D fields uA and uB in one pass sequence: one
+// real-to-complex pass over both, the four strided passes (x on the second
+// stream), one complex-to-real pass of six spectra with both epilogues.
+template <typename T>
+void adv2_stage_impl(Spectral<T>& sp, const T* uA, const AdvEpi<T>& eA, const T* uB, const AdvEpi<T>& eB,
+                     cx<T>* const* Z) {
+  const Grid& g = sp.grid();
+  cudaStream_t s = sp.stream();
+  const cx<T>* tw = sp.twiddles(g.M);
+  const cx<T>* twrc = sp.rc_twiddles();
+  cx<T>* UA = Z[0];
+  cx<T>* XA = Z[1];
+  cx<T>* YA = Z[2];
+  cx<T>* UB = Z[3];
+  cx<T>* XB = Z[4];
+  cx<T>* YB = Z[5];
+  RowsIn<T, 2> in2{{uA, uB}};
+  RowsOut<T, 2> out2{{UA, UB}};
+  r2c<T, 2, false>(g, s, in2, nullptr, out2, 0, tw, twrc);
+  auto epi_bytes = [&](const AdvEpi<T>& e) {
+    return (double)g.N * sizeof(T) *
+           (3 + (e.G[0] ? 3 : 0) + (e.Sout ? 3 + 1 : 0) +
+            (e.out1 ? 3 + ((e.src || e.src_from_a) ? (e.src ? 1 : 0) : (e.gm[0] ? 6 : 0)) + (e.y ? 1 : 0) +
+                          (e.stage == 1 ? 2 : 1)
+                    : 0));
+  };
+  cudaStream_t s2 = sp.aux_stream();
+  REG_CUDA(cudaEventRecord(sp.fork_event(), s));
+  REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
+  deriv<T>(g, sp, 0, UA, XA, nullptr, s2);
+  deriv<T>(g, sp, 0, UB, XB, nullptr, s2);
+  deriv<T>(g, sp, 1, UA, YA, nullptr, s);
+  deriv<T>(g, sp, 1, UB, YB, nullptr, s);
+  REG_CUDA(cudaEventRecord(sp.join_event(), s2));
+  REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
+  DivEpi<T> none{};
+  RowsSpec<T, 6> in6{{XA, YA, UA, XB, YB, UB}};
+  c2r<T, 6, EPI_ADV2>(g, s, in6, (1 << 2) | (1 << 5), eA, none, epi_bytes(eA) + epi_bytes(eB), tw, twrc, eB);
 }
 
 template <typename T>

@@ -175,6 +175,11 @@ struct DivEpi;
 // three packed-spectrum scratch buffers per call (Zx unused in 2D)
 template <typename T>
 void adv_stage(Spectral<T>& sp, const T* u, const fused::AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy);
+// two 3D advection stages (fields uA, uB) sharing their passes; Z: six
+// spectral work arrays of Nc values
+template <typename T>
+void adv2_stage(Spectral<T>& sp, const T* uA, const fused::AdvEpi<T>& eA, const T* uB, const fused::AdvEpi<T>& eB,
+                cx<T>* const* Z);
 // a: d velocity fields at stride N
 template <typename T>
 void div_stage(Spectral<T>& sp, const T* lam, const T* a, const fused::DivEpi<T>& e, cx<T>* Q0, cx<T>* Q1, cx<T>* Q2);

@@ -102,6 +102,8 @@ template <typename T>
 struct Work {
   using C = cx<T>;
   DBuf<C> U, W, X;         // spectra
+  DBuf<C> U2, W2, X2;      // spectra of the second field of a two-field stage
+  DBuf<T> yhS, accS, srcS; // state stage values and one source of the fused forward sweep
   DBuf<T> G, q, va, vb, wa, wb;  // d fields
   DBuf<T> m, yh, acc, k, lam;    // fields
   DBuf<T> vcoef, wcoef;          // coefficient vectors in precision T
@@ -267,6 +269,35 @@ void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* 
   e.h = (T)c->h();
   e.stage = stage;
   adv_stage<T>(spectral<T>(c), u, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
+}
+
+// epilogue of an advection stage without stored-gradient source terms
+template <typename T>
+fused::AdvEpi<T> adv_epi(reg_ctx* c, const T* a, const T* y, T* out1, T* out2, int stage, const T* src = nullptr,
+                         const T* sw = nullptr, T* Sout = nullptr) {
+  const long N = c->N();
+  fused::AdvEpi<T> e{};
+  for (int i = 0; i < c->d; ++i) {
+    e.a[i] = a ? a + i * N : nullptr;
+    e.sw[i] = sw ? sw + i * N : nullptr;
+  }
+  e.src = src;
+  e.Sout = Sout;
+  e.y = y;
+  e.out1 = out1;
+  e.out2 = out2;
+  e.h = (T)c->h();
+  e.stage = stage;
+  return e;
+}
+
+// two 3D advection stages sharing their passes
+template <typename T>
+void adv2(reg_ctx* c, const T* uA, const fused::AdvEpi<T>& eA, const T* uB, const fused::AdvEpi<T>& eB) {
+  Work<T>& w = work<T>(c);
+  const long Nc = c->g.Nc;
+  cx<T>* Z[6] = {w.U.get(Nc), w.W.get(Nc), w.X.get(Nc), w.U2.get(Nc), w.W2.get(Nc), w.X2.get(Nc)};
+  adv2_stage<T>(spectral<T>(c), uA, eA, uB, eB, Z);
 }
 
 // grad u into G (d fields) through the fused stage passes
@@ -560,7 +591,57 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
     for (int j = 0; j <= c->n_t; ++j)
       dot_fields<T>(gm_slot<T>(c, j, 0), vel_node<T>(c, wcoef, j, wa), src + (long)j * N, c->d, N, c->s);
   }
-  for (int seg = 0; seg * K < c->n_t; ++seg) {
+  if (use_src && c->ckpt > 0 && c->d == 3) {
+    // Checkpointed 3D sweep: the state re-advance and the incremental sweep
+    // share their passes. At each t_j one two-field stage runs the state's
+    // stage 1 (with the source s_j = grad m_j . v~(t_j) of its epilogue) and
+    // the incremental stage 2 of step j-1 (which takes s_j from the same
+    // epilogue); a second one runs the state's stage 2 and the incremental
+    // stage 1 of step j (source s_j, kept in one field).
+    T* m = w.m.get(N);
+    T* yhS = w.yhS.get(N);
+    T* accS = w.accS.get(N);
+    T* sj = w.srcS.get(N);
+    for (int seg = 0; seg * K < c->n_t; ++seg) {
+      const int j0 = seg * K, j1 = j0 + K;
+      REG_CUDA(cudaMemcpyAsync(m, w.ck.p + (long)(j0 / c->ckpt) * N, N * sizeof(T), cudaMemcpyDeviceToDevice,
+                               c->s));
+      for (int j = j0; j < j1; ++j) {
+        const T* vA = vel_node<T>(c, vcoef, j, va);
+        const T* wA = vel_node<T>(c, wcoef, j, wa);
+        fused::AdvEpi<T> sA = adv_epi<T>(c, vA, m, yhS, accS, 1, nullptr, wA, sj);
+        if (j == 0) {
+          adv<T>(c, m, vA, nullptr, nullptr, m, yhS, accS, nullptr, 1, nullptr, wA, sj);
+        } else {
+          fused::AdvEpi<T> iB = adv_epi<T>(c, vA, acc, y, nullptr, 2);
+          iB.src_from_a = 1;
+          adv2<T>(c, m, sA, yh, iB);
+          if (mtil)
+            REG_CUDA(cudaMemcpyAsync(mtil + (long)j * N, y, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+        }
+        const T* vB = vel_node<T>(c, vcoef, j + 1, vb);
+        if (j == 0) {
+          adv<T>(c, yhS, vB, nullptr, nullptr, accS, m, nullptr, nullptr, 2);
+          lincomb_t<T>(-h, sj, (T)0, nullptr, yh, N, c->s);
+          lincomb_t<T>((T)(-0.5) * h, sj, (T)0, nullptr, acc, N, c->s);
+        } else {
+          fused::AdvEpi<T> sB = adv_epi<T>(c, vB, accS, m, nullptr, 2);
+          fused::AdvEpi<T> iA = adv_epi<T>(c, vA, y, yh, acc, 1, sj);
+          adv2<T>(c, yhS, sB, y, iA);
+        }
+      }
+    }
+    // the source at t_{n_t} from the final state, and the last incremental stage 2
+    const T* vN = vel_node<T>(c, vcoef, c->n_t, va);
+    fused::AdvEpi<T> sN = adv_epi<T>(c, nullptr, nullptr, nullptr, nullptr, 1, nullptr,
+                                     vel_node<T>(c, wcoef, c->n_t, wa), sj);
+    fused::AdvEpi<T> iN = adv_epi<T>(c, vN, acc, y, nullptr, 2);
+    iN.src_from_a = 1;
+    adv2<T>(c, m, sN, yh, iN);
+    if (mtil)
+      REG_CUDA(cudaMemcpyAsync(mtil + (long)c->n_t * N, y, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  }
+  for (int seg = 0; seg * K < c->n_t && !(use_src && c->ckpt > 0 && c->d == 3); ++seg) {
     int j0 = seg * K, j1 = j0 + K;
     int base = 0;
     if (c->ckpt > 0) {
@@ -734,7 +815,9 @@ size_t graph_signature(reg_ctx* c) {
                         c->w32.fhi.p,  c->w32.flo.p,  c->w64.G.p,    c->w32.G.p,    c->w64.src.p,  c->w32.src.p,
                         c->w64.mtil.p, c->w32.mtil.p, c->w64.lamN.p, c->w32.lamN.p, c->w64.yh2.p, c->w32.yh2.p,
                         c->w64.acc2.p, c->w32.acc2.p, c->w64.st0.p,  c->w32.st0.p,  c->w64.st1.p,  c->w32.st1.p,
-                        c->w64.Gt.p,   c->w32.Gt.p};
+                        c->w64.Gt.p,   c->w32.Gt.p,   c->w64.U2.p,   c->w32.U2.p,   c->w64.W2.p,   c->w32.W2.p,
+                        c->w64.X2.p,   c->w32.X2.p,   c->w64.yhS.p,  c->w32.yhS.p,  c->w64.accS.p, c->w32.accS.p,
+                        c->w64.srcS.p, c->w32.srcS.p};
   size_t h = 1469598103934665603ull;
   for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
   // and the settings that change what the matvec computes
