@@ -59,37 +59,12 @@ __global__ void k_stage(const T* __restrict__ G, const T* __restrict__ vt, const
 }
 
 template <typename T>
-__global__ void k_heun1(const T* __restrict__ k, const T* __restrict__ y, T h, T* __restrict__ yh,
-                        T* __restrict__ acc, long N) {
-  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= N) return;
-  T kv = k[x], yv = y[x];
-  yh[x] = yv + h * kv;
-  acc[x] = yv + (T)0.5 * h * kv;
-}
-
-template <typename T>
-__global__ void k_heun2(const T* __restrict__ k, const T* __restrict__ acc, T h, T* __restrict__ y, long N) {
-  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= N) return;
-  y[x] = acc[x] + (T)0.5 * h * k[x];
-}
-
-template <typename T>
 __global__ void k_dot_fields(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, int d, long N) {
   long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
   T s = 0;
   for (int i = 0; i < d; ++i) s += a[i * N + x] * b[i * N + x];
   out[x] = s;
-}
-
-template <typename T>
-__global__ void k_products(const T* __restrict__ vt, const T* __restrict__ lam, T* __restrict__ q, int d, long N) {
-  long x = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= N) return;
-  T l = lam[x];
-  for (int i = 0; i < d; ++i) q[i * N + x] = vt[i * N + x] * l;
 }
 
 // (f_hi, f_lo)[l][i][x] += c_l lam[x] gm[i][x]; with f_lo null a plain sum
@@ -293,38 +268,12 @@ void transport_stage1(const T* G, const T* vt, const T* gm, const T* wt, const T
   REG_LAUNCH();
 }
 template <typename T>
-void transport_stage2(const T* G, const T* vt, const T* gm, const T* wt, const T* acc, T h, T* ynew, int d, long N,
-                      cudaStream_t s) {
-  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + (gm ? 2 * d : 0) + 2));
-  if (gm) k_stage<T, true, false><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, acc, h, ynew, nullptr, d, N);
-  else k_stage<T, false, false><<<nblk(N), 256, 0, s>>>(G, vt, gm, wt, acc, h, ynew, nullptr, d, N);
-  REG_LAUNCH();
-}
-template <typename T>
-void heun1(const T* k, const T* y, T h, T* yh, T* acc, long N, cudaStream_t s) {
-  ProfScope ps(KK_STAGE, s, 4.0 * N * sizeof(T));
-  k_heun1<T><<<nblk(N), 256, 0, s>>>(k, y, h, yh, acc, N);
-  REG_LAUNCH();
-}
-template <typename T>
-void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s) {
-  ProfScope ps(KK_STAGE, s, 3.0 * N * sizeof(T));
-  k_heun2<T><<<nblk(N), 256, 0, s>>>(k, acc, h, y, N);
-  REG_LAUNCH();
-}
-template <typename T>
 void dot_fields(const T* a, const T* b, T* out, int d, long N, cudaStream_t s) {
   ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + 1));
   k_dot_fields<T><<<nblk(N), 256, 0, s>>>(a, b, out, d, N);
   REG_LAUNCH();
 }
 
-template <typename T>
-void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s) {
-  ProfScope ps(KK_STAGE, s, (double)N * sizeof(T) * (2 * d + 1));
-  k_products<T><<<nblk(N), 256, 0, s>>>(vt, lam, q, d, N);
-  REG_LAUNCH();
-}
 template <typename T>
 void force_acc(T* fhi, T* flo, const T* lam, const T* gm, const Coefs& c, int nc, int d, long N, cudaStream_t s) {
   ProfScope ps(KK_FORCE, s, (double)N * sizeof(T) * ((d + 1) + 2.0 * nc * d * (flo ? 2 : 1)));
@@ -340,11 +289,6 @@ void pair_to_double(const float* hi, const float* lo, double* out, long n, cudaS
 #define INST(T)                                                                                          \
   template void transport_stage1<T>(const T*, const T*, const T*, const T*, const T*, T, T*, T*, int, long, \
                                     cudaStream_t);                                                       \
-  template void transport_stage2<T>(const T*, const T*, const T*, const T*, const T*, T, T*, int, long,     \
-                                    cudaStream_t);                                                       \
-  template void heun1<T>(const T*, const T*, T, T*, T*, long, cudaStream_t);                                \
-  template void heun2<T>(const T*, const T*, T, T*, long, cudaStream_t);                                    \
-  template void products<T>(const T*, const T*, T*, int, long, cudaStream_t);                               \
   template void dot_fields<T>(const T*, const T*, T*, int, long, cudaStream_t);                             \
   template void force_acc<T>(T*, T*, const T*, const T*, const Coefs&, int, int, long, cudaStream_t);
 INST(float)

@@ -22,20 +22,9 @@ void convert(const S* in, T* out, long n, cudaStream_t s);
 template <typename T>
 void transport_stage1(const T* G, const T* vt, const T* gm, const T* wt, const T* y, T h, T* yh, T* acc, int d,
                       long N, cudaStream_t s);
-// Heun stage 2: ynew = acc + h/2 k.
-template <typename T>
-void transport_stage2(const T* G, const T* vt, const T* gm, const T* wt, const T* acc, T h, T* ynew, int d, long N,
-                      cudaStream_t s);
-template <typename T>
-void heun1(const T* k, const T* y, T h, T* yh, T* acc, long N, cudaStream_t s);
-template <typename T>
-void heun2(const T* k, const T* acc, T h, T* y, long N, cudaStream_t s);
 // out = sum_i a_i b_i (d fields at stride N)
 template <typename T>
 void dot_fields(const T* a, const T* b, T* out, int d, long N, cudaStream_t s);
-// q_i = v_i lam
-template <typename T>
-void products(const T* vt, const T* lam, T* q, int d, long N, cudaStream_t s);
 // f[l][i] += c_l lam gm_i: plain sum into fhi (flo null) or a compensated
 // (fhi, flo) pair of precision T
 template <typename T>

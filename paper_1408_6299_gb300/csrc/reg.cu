@@ -321,15 +321,6 @@ void divh(reg_ctx* c, const T* lam, const T* a, const T* y, T* out1, T* out2, in
   div_stage<T>(spectral<T>(c), lam, a, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
 }
 
-// div(v lam) into out
-template <typename T>
-void div_vlam(reg_ctx* c, const T* vt, const T* lam, T* out) {
-  Work<T>& w = work<T>(c);
-  T* q = w.q.get(c->dN());
-  products<T>(vt, lam, q, c->d, c->N(), c->s);
-  spectral<T>(c).div(q, out, w.U.get(c->g.Nc), w.W.get(c->g.Nc));
-}
-
 // ---------------------------------------------------------------------------
 // State solve (Eq. first-order-forward), steps j0..j1-1 from the state in w.m.
 //   gm  (optional): grad m_j into slot (j - base) for j = j0..j1 (the last slot
