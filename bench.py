@@ -20,9 +20,19 @@ One process per GPU (torchrun); with several GPUs every rank runs its own
 replica of the workload (the solver does not shard) and value counts the
 matvecs of all ranks over the slowest rank's time.
 
---impl reference times the CPU oracle (oracle/) on the same workload: each
-step is one oracle matvec on the 256^3 grid with n_t = 2, and the cost of the
-n_t chosen above is extrapolated from the n_t = 1 and n_t = 2 runs.
+--impl reference times the CPU oracle (oracle/) on the same workload. A full
+oracle matvec at n_t = 128 takes minutes, so each step is a bounded sample: one
+oracle matvec on the 256^3 grid with n_t = 2, timed as it runs (ms_per_step is
+that sample's time). value is the rate of full matvecs extrapolated linearly
+in n_t from that sample and one n_t = 1 run (the line says so). With
+--cpu-full the reference arm instead times one whole n_t = 128 oracle matvec
+(steps = 1), the measurement that checks the extrapolation.
+
+Other workloads: --workload batch (the 256-pair 2D batch, sharded across
+ranks), --workload profile (set up the matvec, run one warm-up and one
+measured matvec and print the launch counts SETUP/WARM/MEAS that ncu skips and
+captures), --workload stability --sweep-nt 64,88,128 (per n_t: CFL number and
+mixed-vs-FP64 difference of the matvec).
 """
 import argparse
 import hashlib
@@ -58,7 +68,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-solves", action="store_true")
-    p.add_argument("--workload", default="matvec", choices=["matvec", "batch"])
+    p.add_argument("--workload", default="matvec", choices=["matvec", "batch", "profile", "stability"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="--workload profile only")
+    p.add_argument("--sweep-nt", default="64,88,96,128", help="--workload stability: n_t values")
+    p.add_argument("--cpu-full", action="store_true", help="--impl reference: one whole oracle matvec")
     p.add_argument("--pairs", type=int, default=256)
     p.add_argument("--batch-sample", type=int, default=256)
     p.add_argument("--batch-mode", default="lockstep", choices=["lockstep", "executor"])
@@ -183,24 +196,31 @@ def run_reference(args):
     while cfl > args.cfl:
         n_t *= 2
         cfl /= 2
-    args.n_t = n_t
-    t1 = oracle_matvec_seconds(c, 1)
-    for _ in range(max(0, args.warmup - 1)):
-        oracle_matvec_seconds(c, 2)
-    T, t1, t2s = oracle_extrapolated(c, args.n_t, t1=t1, reps=args.steps)
-    value = 1.0 / T
     cores = O.num_threads()
-    sample = (f"oracle GN matvec on the {args.n}^3 grid with n_t=1 (once) and n_t=2 ({args.steps} timed steps); "
-              f"n_t={args.n_t} cost = t1 + {args.n_t - 1}*(t2 - t1)")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * T, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"random-field {args.n}^3 H2 beta=1e-3 n_c=1 n_t={args.n_t} GN matvec (CPU oracle)",
-                   "grid": [args.n] * 3, "n_t": args.n_t},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
+    base = {"impl": "reference", "metric": METRIC, "unit": UNIT, "n_gpus": args.gpus, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"random-field {args.n}^3 H2 beta=1e-3 n_c=1 n_t={n_t} GN matvec (CPU oracle)",
+                       "grid": [args.n] * 3, "n_t": n_t}}
+    if args.cpu_full:
+        t = oracle_matvec_seconds(c, n_t)
+        value = 1.0 / t
+        sample = f"one whole oracle GN matvec on the {args.n}^3 grid with n_t={n_t}, measured"
+        line = dict(base, value=value, steps=1, warmup=0, ms_per_step=1000.0 * t)
+    else:
+        t1 = oracle_matvec_seconds(c, 1)
+        for _ in range(max(0, args.warmup - 1)):
+            oracle_matvec_seconds(c, 2)
+        t2s = [oracle_matvec_seconds(c, 2) for _ in range(args.steps)]
+        t2 = statistics.median(t2s)
+        T = t1 + (n_t - 1) * max(t2 - t1, 1e-9)
+        value = 1.0 / T
+        sample = (f"each step: one oracle GN matvec on the {args.n}^3 grid with n_t=2 ({t2:.2f} s median, the "
+                  f"step's measured time); value extrapolated to n_t={n_t} as t1 + {n_t - 1}*(t2 - t1) with "
+                  f"t1 = {t1:.2f} s (n_t=1)")
+        line = dict(base, value=value, steps=args.steps, warmup=args.warmup, ms_per_step=1000.0 * t2,
+                    extrapolated_ms_per_matvec=1000.0 * T)
+    line["cpu_baseline"] = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line["e2e"] = {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     print(json.dumps(line), flush=True)
 
 
@@ -339,6 +359,64 @@ def run_batch(args):
 
 
 # ----------------------------------------------------------------------------
+# helpers for ncu captures and the Heun stability table (profiles/)
+# ----------------------------------------------------------------------------
+def matvec_context(c, n_t, prec, ckpt):
+    import numpy as np
+    import torch
+
+    from paper_1408_6299_gb300 import lib
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+    v, mT = dev(c["v_true"]), dev(c["mT"])
+    R = lib.Registration(c["n"], n_t, 1, c["beta"], c["reg"], c["stokes"], prec, ckpt)
+    mR = torch.empty(c["n"], dtype=torch.float64, device="cuda")
+    R.transport(v, mT, mR)
+    R.set_images(mT, mR)
+    R.linearize(v)
+    return R, v, dev(c["vt"])
+
+
+def run_profile(args):
+    """one warm-up and one measured matvec; prints the launch counts to skip
+    (SETUP + WARM) and to capture (MEAS) with ncu"""
+    import torch
+
+    from paper_1408_6299_gb300 import lib, synth
+    c = synth.random_3d(args.n)
+    prec = lib.REG_MIXED if args.precision == "mixed" else lib.REG_FP64
+    R, v, vt = matvec_context(c, args.n_t, prec, args.ckpt)
+    H = torch.empty((1, 3) + c["n"], dtype=torch.float64, device="cuda")
+    l0 = lib.launch_count()
+    R.hessvec(vt, H)
+    l1 = lib.launch_count()
+    R.hessvec(vt, H)
+    l2 = lib.launch_count()
+    torch.cuda.synchronize()
+    print(f"SETUP={l0} WARM={l1 - l0} MEAS={l2 - l1}", flush=True)
+
+
+def run_stability(args):
+    """per n_t: CFL number and relative 2-norm difference of the mixed and FP64 matvecs"""
+    import torch
+
+    from paper_1408_6299_gb300 import lib, synth
+    c = synth.random_3d(args.n)
+    for n_t in [int(x) for x in args.sweep_nt.split(",")]:
+        out = {}
+        for prec in (lib.REG_FP64, lib.REG_MIXED):
+            R, v, vt = matvec_context(c, n_t, prec, args.ckpt)
+            H = torch.empty((1, 3) + c["n"], dtype=torch.float64, device="cuda")
+            R.hessvec(vt, H)
+            out[prec] = H
+            cfl = R.cfl(v)
+            R.close()
+        err = float(torch.linalg.vector_norm(out[1] - out[0]) / torch.linalg.vector_norm(out[0]))
+        print(f"n_t={n_t} cfl={cfl:.4f} mixed_vs_fp64={err:.3e} "
+              f"norm_fp64={float(torch.linalg.vector_norm(out[0])):.6e} "
+              f"norm_mixed={float(torch.linalg.vector_norm(out[1])):.6e}", flush=True)
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args):
@@ -446,7 +524,23 @@ def run_ours(args):
         torch.cuda.synchronize()
         fp64_s = (time.perf_counter() - t0) / args.fp64_steps
         mixed_err = float(torch.linalg.vector_norm(Hv - H64) / torch.linalg.vector_norm(H64))
-        fp64 = {"value": 1.0 / fp64_s, "unit": UNIT, "mixed_vs_fp64_rel_err": mixed_err}
+        # the FP64 form against both of its roofs: HBM and the measured FP64 FMA rate
+        R64.profile_begin()
+        R64.hessvec(vt, H64)
+        p64 = R64.profile_end()
+        dom64 = max(p64, key=lambda k: p64[k]["ms"])
+        k64 = p64[dom64]
+        peak64 = lib.fp64_peak_gflops()
+        hbm_peak, _ = measured_peaks()
+        fl_rate = k64["flops"] / (k64["ms"] / 1000.0) / 1e9 if k64["ms"] > 0 else 0.0
+        by_rate = k64["bytes"] / (k64["ms"] / 1000.0) / 1e9 if k64["ms"] > 0 else 0.0
+        fp64 = {"value": 1.0 / fp64_s, "unit": UNIT, "mixed_vs_fp64_rel_err": mixed_err,
+                "roofline": {"kernel": dom64, "share_of_matvec": k64["ms"] / max(sum(x["ms"] for x in p64.values()), 1e-9),
+                             "fp64_gflops_achieved": fl_rate, "fp64_gflops_peak": peak64,
+                             "fp64_frac": fl_rate / peak64 if peak64 > 0 else None,
+                             "fp64_peak_source": "measured live (reg_fp64_peak: FMA chains, CUDA events)",
+                             "hbm_gbs_achieved": by_rate, "hbm_frac": by_rate / hbm_peak,
+                             "flops_counted": "FFT butterflies, twiddles, multipliers and packing (radix-plan counts)"}}
         R64.close()
 
     # the same matvec with the whole state trajectory stored (no recomputation)
@@ -523,9 +617,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         T, t1, t2s = oracle_extrapolated(c, n_t)
-        cpu = {"value": 1.0 / T, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-               "sample": f"oracle GN matvec on the {args.n}^3 grid with n_t=1 ({t1:.1f} s) and n_t=2 "
-                         f"({t2s[0]:.1f} s); n_t={n_t} cost extrapolated as t1 + {n_t - 1}*(t2 - t1)"}
+        cpu = {"value": 1.0 / T, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "extrapolated": True,
+               "sample": f"oracle GN matvec on the {args.n}^3 grid measured with n_t=1 ({t1:.1f} s) and n_t=2 "
+                         f"({t2s[0]:.1f} s); the n_t={n_t} matvec is extrapolated linearly in n_t as "
+                         f"t1 + {n_t - 1}*(t2 - t1) = {T:.1f} s (bench.py --impl reference --cpu-full measures one)"}
 
     if rank == 0:
         line = {
@@ -536,7 +631,8 @@ def run_ours(args):
                                    f"state checkpoints every {args.ckpt}",
                        "grid": [args.n] * 3, "n_t": n_t, "n_t_rule": f"doubled from {nt_cfg} until CFL <= {args.cfl}",
                        "cfl": cfl, "ckpt_every": args.ckpt,
-                       "precision": "mixed (f32 sweeps, f64 force/tail/vectors)",
+                       "precision": "mixed (f32 sweeps; body force accumulated as a compensated f32 pair; "
+                                    "f64 tail and Krylov vectors)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "clocks": ck, "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "fp64": fp64,
             "store_all": store_all, "newton": newton, "as_configured": as_cfg, "solve_to_rel_grad_1e-2": solves, "batch_2d": batch, "cpu_baseline": cpu,
@@ -556,6 +652,10 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "profile":
+        run_profile(args)
+    elif args.workload == "stability":
+        run_stability(args)
     else:
         run_ours(args)
 

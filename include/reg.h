@@ -156,7 +156,7 @@ REG_API reg_status reg_precond(reg_ctx* ctx, const double* r, double* z);
  * until the process exits; it calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *   r, z: device pointers, n_c*d*N doubles each (z may equal r).
- *   Limit: n_c*d*N/2 <= 2,095,040 (for example 3D 64^3 with n_c <= 3, 2D
+ *   Limit: n_c*d*N/2 <= 2,095,040 (for example 3D 64^3 with n_c <= 5, 2D
  *   512^2 with n_c <= 7); larger problems get REG_EINVAL and a message in
  *   reg_last_error(NULL).
  *   The first call on a device does a set-up with that device current: it
@@ -406,6 +406,21 @@ REG_API reg_status reg_profile_begin(reg_ctx* ctx, unsigned kind_mask);
  * the summed event time in ms, the summed algorithmic bytes (the bytes each
  * launch must read and write) and the number of launches. Synchronises. */
 REG_API reg_status reg_profile_end(reg_ctx* ctx, double* ms, double* bytes, long* count);
+
+/* Floating-point operations of the transforms of the launches collected by
+ * the last reg_profile_end, per kind (REG_KIND_COUNT values): the butterflies
+ * and twiddle multiplications of every FFT the launches ran (radix plan
+ * counts), the spectral multipliers of the column passes, and the packing of
+ * the real-to-complex rows. Pointwise epilogue arithmetic is not counted. */
+REG_API reg_status reg_profile_flops(reg_ctx* ctx, double* flops);
+
+/* Double-precision FMA throughput of the current device in GFLOP/s (2 flops
+ * per FMA): independent FMA chains in every thread of one wave of resident
+ * blocks, the best of three launches timed with CUDA events after a warm-up.
+ * Allocates and frees a small buffer; changes no device setting. The bound
+ * of the FP64 transport sweeps, whose arithmetic rate the bench reports
+ * against it. Errors: REG_ECUDA (message in reg_last_error(NULL)). */
+REG_API reg_status reg_fp64_peak(double* gflops);
 
 /* Number of kernel launches issued by the library in this process so far. */
 REG_API long reg_launch_count(void);

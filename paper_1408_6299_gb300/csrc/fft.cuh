@@ -99,6 +99,32 @@ template <> struct Plan<128> { static constexpr int S = 2; static constexpr int 
 template <> struct Plan<256> { static constexpr int S = 2; static constexpr int R[3] = {16, 16, 1}; };
 template <> struct Plan<512> { static constexpr int S = 3; static constexpr int R[3] = {8, 8, 8}; };
 
+// Real floating-point operations of Dft<T,R>::run: two half-size DFTs, R
+// complex additions and one complex multiplication (6 operations) per
+// constant twiddle that is not a multiple of -i.
+__host__ __device__ constexpr double dft_flops(int R) {
+  if (R <= 1) return 0.0;
+  int general = 0;
+  for (int k = 0; k < R / 2; ++k)
+    if (((k * 16 / R) % 16) % 4 != 0) ++general;
+  return 2.0 * dft_flops(R / 2) + 2.0 * R + 6.0 * general;
+}
+
+// Real floating-point operations of one forward transform of length L along
+// the radix plan: the butterflies of every stage and the complex twiddle
+// multiplications between stages (counted for every stage after the first,
+// trivial table entries included, as the kernels execute them).
+template <int L>
+constexpr double fft_flops() {
+  using P = Plan<L>;
+  double f = 0.0;
+  for (int s = 0; s < P::S; ++s) {
+    f += (double)(L / P::R[s]) * dft_flops(P::R[s]);
+    if (s > 0) f += (double)(L / P::R[s]) * (P::R[s] - 1) * 6.0;
+  }
+  return f;
+}
+
 // Offset of stage s's twiddle block inside the table of length L. Stage s
 // (radix R, Ns previous) stores W_{Ns R}^{r k} at [r*Ns + k], r < R, k < Ns.
 // Stage 0 needs none.

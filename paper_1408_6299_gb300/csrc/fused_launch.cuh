@@ -28,7 +28,8 @@ void r2c_L(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam,
   // against 1024 and 8192 on the 256^3 matvec
   constexpr int RB0 = row_elems<T>() / (pow2_ceil(NF) * M * (sizeof(T) == 4 && NF == 1 ? 2 : 1));
   constexpr int RB = RB0 < 1 ? 1 : RB0;
-  ProfScope ps(KK_ROWS_R2C, s, (double)g.N * sizeof(T) * (2 * NF + (PROD ? 1 : 0)));
+  ProfScope ps(KK_ROWS_R2C, s, (double)g.N * sizeof(T) * (2 * NF + (PROD ? 1 : 0)),
+               (double)g.rows * NF * (fft_flops<M>() + 8.0 * M));
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
   k_rows_r2c_n<T, L, RB, NF, PROD><<<grid, kThreads, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
   REG_LAUNCH();
@@ -60,7 +61,7 @@ void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, 
   constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NF == 1 || NF > 4 ? 8 : 4) * M)
                                      : row_elems<T>() / ((NF > 4 ? 8 : pow2_ceil(NF)) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
-  ProfScope ps(KK_ROWS_C2R, s, bytes);
+  ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * NF * (fft_flops<M>() + 8.0 * M));
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
   k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc, advB);
   REG_LAUNCH();
@@ -85,7 +86,8 @@ void c2r(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, co
 template <typename T, int L, int TC>
 void deriv_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long outer, const cx<T>* tw,
                   cudaStream_t st) {
-  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0));
+  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0),
+               (double)s * outer * (2.0 * fft_flops<L>() + L * (add ? 4.0 : 2.0)));
   dim3 grid((unsigned)(s / TC), (unsigned)outer);
   k_cols_deriv<T, L, TC><<<grid, kThreads, 0, st>>>(in, out, add, s, tw);
   REG_LAUNCH();
@@ -149,7 +151,8 @@ void deriv2_launch(const cx<T>* in, cx<T>* out, const cx<T>* add, long s, long o
                    cudaStream_t st) {
   constexpr int R0 = Plan<L>::R[0], R1 = Plan<L>::R[1];
   constexpr int NT = TC * (R0 > L / R0 ? R0 : L / R0);
-  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0));
+  ProfScope ps(KK_COLS, st, (double)s * outer * L * sizeof(cx<T>) * (add ? 3.0 : 2.0),
+               (double)s * outer * (2.0 * fft_flops<L>() + L * (add ? 4.0 : 2.0)));
   const long ntx = s / TC, ntiles = ntx * outer;
   if constexpr (PERSIST) {
     constexpr size_t smem = 2 * (size_t)L * TC * sizeof(cx<T>);
@@ -385,7 +388,10 @@ void adv2_stage_impl(Spectral<T>& sp, const T* uA, const AdvEpi<T>& eA, const T*
   REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
   DivEpi<T> none{};
   RowsSpec<T, 6> in6{{XA, YA, UA, XB, YB, UB}};
-  c2r<T, 6, EPI_ADV2>(g, s, in6, (1 << 2) | (1 << 5), eA, none, epi_bytes(eA) + epi_bytes(eB), tw, twrc, eB);
+  // a velocity read by both epilogues (the same node, or n_c = 1) is counted once
+  const bool shared_a = eA.out1 && eB.out1 && eA.a[0] == eB.a[0];
+  const double bytes = epi_bytes(eA) + epi_bytes(eB) - (shared_a ? 3.0 * g.N * sizeof(T) : 0.0);
+  c2r<T, 6, EPI_ADV2>(g, s, in6, (1 << 2) | (1 << 5), eA, none, bytes, tw, twrc, eB);
 }
 
 template <typename T>

@@ -56,23 +56,25 @@ struct KernelProfiler {
   struct Rec {
     int kind;
     cudaEvent_t a, b;
-    double bytes;
+    double bytes, flops;
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  double last_flops[KK_COUNT] = {0};  // per kind, of the last collected window
   ~KernelProfiler();
   cudaEvent_t take();
   void collect(double* ms, double* bytes, long* count);  // synchronises
 };
 extern thread_local KernelProfiler* tl_prof;
 
-// bracket one launch; bytes = algorithmic bytes moved by it
+// bracket one launch; bytes = algorithmic bytes moved by it, flops = the
+// floating-point operations of its transforms (0 where not counted)
 struct ProfScope {
   int kind;
   cudaStream_t s;
-  double bytes;
+  double bytes, flops;
   cudaEvent_t a = nullptr;
-  ProfScope(int k, cudaStream_t st, double b);
+  ProfScope(int k, cudaStream_t st, double b, double f = 0.0);
   ~ProfScope();
 };
 

@@ -112,13 +112,15 @@ bool chebyshev_gram_inverse(int nc, double* Ci) {
   return true;
 }
 
-bool is_device(const void* p) {
+// memory the kernels on device `dev` may address: device memory of that
+// device, or managed memory
+bool is_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     (void)cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace
@@ -140,10 +142,11 @@ reg_status reg_precond_noalloc(int d, const int64_t* n, int n_c, double beta, in
       return noalloc_fail(REG_EINVAL, "n_c*d*N/2 = " + std::to_string(ncd * g.Nc) +
                                           " spectral values exceed the fixed scratch capacity of " +
                                           std::to_string(kCapacity) + " (64 MiB per GPU); use reg_precond");
-    if (!is_device(r) || !is_device(z)) return noalloc_fail(REG_EINVAL, "r and z must be device pointers");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(REG_ECUDA, cudaGetErrorString(e));
+    if (!is_device(r, dev) || !is_device(z, dev))
+      return noalloc_fail(REG_EINVAL, "r and z must be device (or managed) memory of the current device");
     if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(REG_EINVAL, "device ordinal out of range");
     int st = setup_device(dev);
     if (st != 0) return noalloc_fail(REG_ECUDA, cudaGetErrorString((cudaError_t)st));

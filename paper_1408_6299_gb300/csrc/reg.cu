@@ -182,6 +182,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // host/device pointer handling
 // ---------------------------------------------------------------------------
+// true for memory the kernels can address directly (device memory of the
+// current device, or managed memory), false for host memory (staged through
+// the context's buffers); device memory of another device is refused, since
+// kernels launched on the current device would fault on it
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -189,7 +193,14 @@ bool is_device_ptr(const void* p) {
     (void)cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int dev = 0;
+  REG_CUDA(cudaGetDevice(&dev));
+  if (a.device != dev)
+    throw StatusError{REG_EINVAL, "array argument lives on device " + std::to_string(a.device) + " but device " +
+                                      std::to_string(dev) + " is current"};
+  return true;
 }
 
 const double* input_ptr(reg_ctx* c, const double* p, long n, int slot) {
@@ -2126,6 +2137,13 @@ reg_status reg_profile_end(reg_ctx* ctx, double* ms, double* bytes, long* count)
     if (bytes) bytes[k] = b[k];
     if (count) count[k] = n[k];
   }
+  API_END
+}
+
+reg_status reg_profile_flops(reg_ctx* ctx, double* flops) {
+  API_BEGIN(ctx)
+  if (!flops) throw StatusError{REG_EINVAL, "flops is null"};
+  for (int k = 0; k < KK_COUNT; ++k) flops[k] = c_->prof.last_flops[k];
   API_END
 }
 

@@ -393,7 +393,8 @@ std::vector<double> stage_table(int L) {
 template <typename T, int L, int RB>
 void launch_rows(bool inverse, const void* in, void* out, long nrows, const cx<T>* tw, const cx<T>* twrc,
                  cudaStream_t s) {
-  ProfScope ps(inverse ? KK_ROWS_C2R : KK_ROWS_R2C, s, 2.0 * (double)nrows * L * sizeof(T));
+  ProfScope ps(inverse ? KK_ROWS_C2R : KK_ROWS_R2C, s, 2.0 * (double)nrows * L * sizeof(T),
+               (double)nrows * (fft_flops<L / 2>() + 8.0 * (L / 2)));
   dim3 grid((unsigned)((nrows + RB - 1) / RB));
   if (!inverse)
     k_rows_r2c<T, L, RB><<<grid, kThreads, 0, s>>>((const T*)in, (cx<T>*)out, nrows, tw, twrc);
@@ -421,7 +422,7 @@ void dispatch_rows(int L, bool inverse, const void* in, void* out, long nrows, c
 
 template <typename T, int L, int TC>
 void launch_cols(cx<T>* U, long s, long outer, const cx<T>* tw, bool inverse, cudaStream_t st) {
-  ProfScope ps(KK_COLS, st, 2.0 * (double)s * outer * L * sizeof(cx<T>));
+  ProfScope ps(KK_COLS, st, 2.0 * (double)s * outer * L * sizeof(cx<T>), (double)s * outer * fft_flops<L>());
   dim3 grid((unsigned)(s / TC), (unsigned)outer);
   k_cols<T, L, TC><<<grid, kThreads, 0, st>>>(U, s, tw, inverse ? 1 : 0);
   REG_LAUNCH();
@@ -690,6 +691,7 @@ void KernelProfiler::collect(double* ms, double* bytes, long* count) {
     ms[k] = 0;
     bytes[k] = 0;
     count[k] = 0;
+    last_flops[k] = 0;
   }
   for (auto& r : recs) {
     REG_CUDA(cudaEventSynchronize(r.b));
@@ -697,6 +699,7 @@ void KernelProfiler::collect(double* ms, double* bytes, long* count) {
     REG_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
     ms[r.kind] += t;
     bytes[r.kind] += r.bytes;
+    last_flops[r.kind] += r.flops;
     count[r.kind] += 1;
     pool.push_back(r.a);
     pool.push_back(r.b);
@@ -704,7 +707,7 @@ void KernelProfiler::collect(double* ms, double* bytes, long* count) {
   recs.clear();
 }
 
-ProfScope::ProfScope(int k, cudaStream_t st, double b) : kind(k), s(st), bytes(b) {
+ProfScope::ProfScope(int k, cudaStream_t st, double b, double f) : kind(k), s(st), bytes(b), flops(f) {
   if (tl_prof && (tl_prof->mask & (1u << k))) {
     a = tl_prof->take();
     REG_CUDA(cudaEventRecord(a, s));
@@ -715,7 +718,7 @@ ProfScope::~ProfScope() {
   if (!a || !tl_prof) return;
   cudaEvent_t b = tl_prof->take();
   if (cudaEventRecord(b, s) != cudaSuccess) return;
-  tl_prof->recs.push_back(KernelProfiler::Rec{kind, a, b, bytes});
+  tl_prof->recs.push_back(KernelProfiler::Rec{kind, a, b, bytes, flops});
 }
 
 }  // namespace reg

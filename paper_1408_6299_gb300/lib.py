@@ -188,6 +188,8 @@ _SIGNATURES = {
                            ctypes.POINTER(SolveReport), ctypes.c_int],
     "reg_profile_begin": [_vp, ctypes.c_uint],
     "reg_profile_end": [_vp, _vp, _vp, _vp],
+    "reg_profile_flops": [_vp, _vp],
+    "reg_fp64_peak": [ctypes.POINTER(ctypes.c_double)],
 }
 
 EXPORTED = tuple(_SIGNATURES) + ("reg_last_error", "reg_solve_opts_default", "reg_launch_count",
@@ -209,6 +211,16 @@ def launch_count():
     return int(load().reg_launch_count())
 
 
+def fp64_peak_gflops():
+    """Measured double-precision FMA throughput of the current device (GFLOP/s)."""
+    L = load()
+    g = ctypes.c_double(0.0)
+    st = L.reg_fp64_peak(ctypes.byref(g))
+    if st != REG_OK:
+        raise RegError(st, L.reg_last_error(None).decode())
+    return g.value
+
+
 def precond_noalloc(n, n_c, beta, reg, r, z, stream=None):
     """z = P^{-1} r like Registration.precond, without a context and without
     allocating (fixed device scratch; r and z must be CUDA tensors). Returns
@@ -216,8 +228,9 @@ def precond_noalloc(n, n_c, beta, reg, r, z, stream=None):
     L = load()
     n = tuple(int(k) for k in n)
     arr = (ctypes.c_int64 * len(n))(*n)
-    a, ka = _addr(r)
-    b, kb = _addr(z)
+    count = int(n_c) * len(n) * int(np.prod(n))
+    a, ka = _addr(r, count)
+    b, kb = _addr(z, count)
     st = L.reg_precond_noalloc(len(n), arr, int(n_c), float(beta), int(reg), a, b, stream)
     if st != REG_OK:
         raise RegError(st, L.reg_last_error(None).decode())
@@ -228,9 +241,10 @@ def _problem_array(problems):
     keep = []
     for i, p in enumerate(problems):
         n = tuple(int(k) for k in p["n"])
-        a, ka = _addr(p["mT"])
-        b, kb = _addr(p["mR"])
-        c, kc = _addr(p["v"])
+        N = int(np.prod(n))
+        a, ka = _addr(p["mT"], N)
+        b, kb = _addr(p["mR"], N)
+        c, kc = _addr(p["v"], int(p.get("n_c", 1)) * len(n) * N)
         keep += [ka, kb, kc]
         arr[i] = ProblemC(len(n), (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n)))), int(p["n_t"]),
                           int(p.get("n_c", 1)), float(p["beta"]), int(p.get("reg", REG_H1)),
@@ -297,23 +311,35 @@ def load(build_if_needed: bool = True):
     return _lib
 
 
-def _addr(a):
-    """(address, keepalive) of a contiguous float64 torch tensor or numpy array."""
+def _addr(a, count=None):
+    """(address, keepalive) of a contiguous float64 torch tensor or numpy array.
+
+    count: the number of float64 values the library will read or write
+    through this pointer; a different element count raises ValueError before
+    any library call (the C side cannot know the size of the array). A CUDA
+    tensor must live on the current device, where the kernels run."""
     if a is None:
         return None, None
+    n = None
     try:
         import torch
         if isinstance(a, torch.Tensor):
             if a.dtype != torch.float64 or not a.is_contiguous():
                 raise TypeError("tensors passed to the registration library must be contiguous float64")
-            return a.data_ptr(), a
+            if a.is_cuda and a.device.index != torch.cuda.current_device():
+                raise ValueError(f"tensor on {a.device} but cuda:{torch.cuda.current_device()} is current")
+            n, out = a.numel(), (a.data_ptr(), a)
     except ImportError:
         pass
-    if isinstance(a, np.ndarray):
+    if n is None:
+        if not isinstance(a, np.ndarray):
+            raise TypeError(f"unsupported array type {type(a)}")
         if a.dtype != np.float64 or not a.flags.c_contiguous:
             raise TypeError("arrays passed to the registration library must be C-contiguous float64")
-        return a.ctypes.data, a
-    raise TypeError(f"unsupported array type {type(a)}")
+        n, out = a.size, (a.ctypes.data, a)
+    if count is not None and n != int(count):
+        raise ValueError(f"array of {n} float64 values where {int(count)} are expected")
+    return out
 
 
 class Registration:
@@ -325,6 +351,7 @@ class Registration:
         self.n = tuple(int(k) for k in n)
         self.d = len(self.n)
         self.n_t, self.n_c = int(n_t), int(n_c)
+        self.ckpt_every = int(ckpt_every)
         ctx = _vp()
         arr = (ctypes.c_int64 * self.d)(*self.n)
         st = self.L.reg_create(ctypes.byref(ctx), self.d, arr, self.n_t, self.n_c, float(beta), int(reg),
@@ -340,6 +367,11 @@ class Registration:
     @property
     def N(self):
         return int(np.prod(self.n))
+
+    @property
+    def ncdN(self):
+        """values of a coefficient vector: n_c * d * N"""
+        return self.n_c * self.d * self.N
 
     def coef_shape(self):
         return (self.n_c, self.d) + self.n
@@ -365,93 +397,93 @@ class Registration:
         self._check(self.L.reg_set_hessian(self.ctx, int(kind)))
 
     def set_images(self, mT, mR):
-        a, ka = _addr(mT)
-        b, kb = _addr(mR)
+        a, ka = _addr(mT, self.N)
+        b, kb = _addr(mR, self.N)
         self._check(self.L.reg_set_images(self.ctx, a, b))
 
     def objective(self, v):
-        a, ka = _addr(v)
+        a, ka = _addr(v, self.ncdN)
         J = ctypes.c_double()
         parts = (ctypes.c_double * 2)()
         self._check(self.L.reg_objective(self.ctx, a, ctypes.byref(J), parts))
         return J.value, (parts[0], parts[1])
 
     def gradient(self, v, g):
-        a, ka = _addr(v)
-        b, kb = _addr(g)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(g, self.ncdN)
         J = ctypes.c_double()
         self._check(self.L.reg_gradient(self.ctx, a, b, ctypes.byref(J)))
         return J.value
 
     def linearize(self, v):
-        a, ka = _addr(v)
+        a, ka = _addr(v, self.ncdN)
         self._check(self.L.reg_linearize(self.ctx, a))
 
     def hessvec(self, vt, out):
-        a, ka = _addr(vt)
-        b, kb = _addr(out)
+        a, ka = _addr(vt, self.ncdN)
+        b, kb = _addr(out, self.ncdN)
         self._check(self.L.reg_hessvec(self.ctx, a, b))
 
     def precond(self, r, z):
-        a, ka = _addr(r)
-        b, kb = _addr(z)
+        a, ka = _addr(r, self.ncdN)
+        b, kb = _addr(z, self.ncdN)
         self._check(self.L.reg_precond(self.ctx, a, b))
 
     def regularization(self, v, out):
-        a, ka = _addr(v)
-        b, kb = _addr(out)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(out, self.ncdN)
         self._check(self.L.reg_regularization(self.ctx, a, b))
 
     def transport(self, v, m0, m1):
-        a, ka = _addr(v)
-        b, kb = _addr(m0)
-        c, kc = _addr(m1)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(m0, self.N)
+        c, kc = _addr(m1, self.N)
         self._check(self.L.reg_transport(self.ctx, a, b, c))
 
     def transport_adjoint(self, v, m0, G, grad_v=None, grad_m0=None):
-        a, ka = _addr(v)
-        b, kb = _addr(m0)
-        c, kc = _addr(G)
-        d, kd = _addr(grad_v)
-        e, ke = _addr(grad_m0)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(m0, self.N)
+        c, kc = _addr(G, self.N)
+        d, kd = _addr(grad_v, self.ncdN)
+        e, ke = _addr(grad_m0, self.N)
         self._check(self.L.reg_transport_adjoint(self.ctx, a, b, c, d, e))
 
     def detF(self, v, substeps=1, out=None):
-        a, ka = _addr(v)
-        b, kb = _addr(out)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(out, self.N)
         st = (ctypes.c_double * 4)()
         self._check(self.L.reg_detF(self.ctx, a, int(substeps), st, b))
         return tuple(st)
 
     def cfl(self, v):
-        a, ka = _addr(v)
+        a, ka = _addr(v, self.ncdN)
         c = ctypes.c_double()
         self._check(self.L.reg_cfl(self.ctx, a, ctypes.byref(c)))
         return c.value
 
     def grid_angle(self, v, substeps=1, out=None):
         """Smallest acute angle between deformed grid edges: (min, max, mean, std)."""
-        a, ka = _addr(v)
-        b, kb = _addr(out)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(out, self.N)
         st = (ctypes.c_double * 4)()
         self._check(self.L.reg_grid_angle(self.ctx, a, int(substeps), st, b))
         return tuple(st)
 
     def displacement(self, v, u):
         """u_1 of the deformation map into u (d fields)."""
-        a, ka = _addr(v)
-        b, kb = _addr(u)
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(u, self.d * self.N)
         self._check(self.L.reg_displacement(self.ctx, a, b))
 
     def smooth(self, sigma, m, out):
         """Gaussian presmoothing of m (N values) into out."""
-        a, ka = _addr(m)
-        b, kb = _addr(out)
+        a, ka = _addr(m, self.N)
+        b, kb = _addr(out, self.N)
         self._check(self.L.reg_smooth(self.ctx, float(sigma), a, b))
 
     def lanczos(self, q0, k, precond=False):
         """(alpha, beta, ritz) of k Lanczos steps on H (or P^{-1} H) at the linearisation point."""
-        a, ka = _addr(q0)
+        a, ka = _addr(q0, self.ncdN)
         al = (ctypes.c_double * k)()
         be = (ctypes.c_double * k)()
         rz = (ctypes.c_double * k)()
@@ -469,6 +501,7 @@ class Registration:
 
     def continuation(self, v, solve_opts=None, **cont):
         """Beta continuation in place on v; returns the report dict."""
+        a, ka = _addr(v, self.ncdN)
         so = SolveOpts.make(self.L, solve_opts or {})
         co = ContOpts()
         self.L.reg_cont_opts_default(ctypes.byref(co))
@@ -477,7 +510,6 @@ class Registration:
             if k not in names:
                 raise TypeError(f"unknown continuation option {k!r}")
             setattr(co, k, val)
-        a, ka = _addr(v)
         rep = ContReport()
         self._check(self.L.reg_continuation(self.ctx, a, ctypes.byref(so), ctypes.byref(co), ctypes.byref(rep)))
         out = rep.as_dict()
@@ -492,12 +524,14 @@ class Registration:
         by = (ctypes.c_double * 7)()
         cnt = (ctypes.c_long * 7)()
         self._check(self.L.reg_profile_end(self.ctx, ms, by, cnt))
-        return {KIND_NAMES[k]: dict(ms=ms[k], bytes=by[k], launches=cnt[k]) for k in range(7)}
+        fl = (ctypes.c_double * 7)()
+        self._check(self.L.reg_profile_flops(self.ctx, fl))
+        return {KIND_NAMES[k]: dict(ms=ms[k], bytes=by[k], launches=cnt[k], flops=fl[k]) for k in range(7)}
 
     def solve(self, v, **opts):
         """Solve in place on v; returns the report dict (raises on a failed solve)."""
+        a, ka = _addr(v, self.ncdN)
         o = SolveOpts.make(self.L, opts)
-        a, ka = _addr(v)
         rep = SolveReport()
         st = self.L.reg_solve(self.ctx, a, ctypes.byref(o), ctypes.byref(rep))
         out = rep.as_dict()

@@ -14,6 +14,8 @@ row-major, last axis fastest. Velocity coefficient arrays have shape
 Band-limited random fields are drawn as Hermitian Gaussian Fourier
 coefficients (numpy's FFT synthesises them); every mode that touches an
 axis's Nyquist index is zero, and so is the k = 0 mode unless asked for.
+White-noise fields (independent Gaussian values per grid point) carry the
+full spectrum instead, Nyquist modes included.
 """
 from __future__ import annotations
 
@@ -52,6 +54,22 @@ def random_spectral_field(n, rng, kmax, slope=0.0, keep_mean=False):
         nyq |= np.abs(K[a]) == k // 2
     amp[nyq] = 0.0
     return np.fft.irfftn(coef * amp, s=n, axes=tuple(range(len(n))))
+
+
+def white_noise(n, rng, scale=1.0):
+    """Independent standard normal values per grid point times scale: every
+    Fourier mode, the Nyquist modes of each axis included, is present."""
+    return scale * rng.standard_normal(tuple(int(k) for k in n))
+
+
+def white_noise_velocity(n, rng, n_c, max_speed):
+    """n_c white-noise coefficient fields of d components each, scaled so that
+    the largest point speed sum_l |v_l(x)|_2 is max_speed (a bound on the
+    speed at every time, since every Chebyshev polynomial is bounded by one)."""
+    n = tuple(int(k) for k in n)
+    v = rng.standard_normal((n_c, len(n)) + n)
+    speed = np.sqrt((v ** 2).sum(axis=1)).sum(axis=0).max()
+    return v * (max_speed / speed)
 
 
 def _curl_spectral(n, potentials):

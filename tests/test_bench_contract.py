@@ -22,3 +22,13 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["grid"] == [16, 16, 16]
+    # each step is the sample it times: ms_per_step is the measured sample time
+    assert d["ms_per_step"] < d["extrapolated_ms_per_matvec"]
+
+
+def test_reference_arm_whole_matvec():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cpu-full",
+                          "--n", "16", "--n_t", "4"], capture_output=True, text=True, timeout=300, cwd=ROOT,
+                         check=True).stdout
+    d = json.loads([ln for ln in out.splitlines() if ln.startswith("{")][0])
+    assert d["steps"] == 1 and abs(d["value"] * d["ms_per_step"] / 1000.0 - 1.0) < 1e-9

@@ -216,3 +216,93 @@ def test_extreme_grid_shapes(n):
         Hv = empty(R.coef_shape())
         R.hessvec(cuda(vt), Hv)
         assert rel(host(Hv), P.hessvec(0.5 * v, mT, vt)) < tol, (n, precision)
+
+
+# ---------------------------------------------------------------------------
+# Checkpointed contexts: the gradient and the transport adjoint recompute the
+# state segment by segment from every K-th state (Alg. 1 with time
+# checkpointing); the result must not depend on K.
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def ckpt_cases():
+    out = [(synth.sinusoid_2d(32), "sin32"), (synth.stokes_3d(16, n_t=8, n_c=3), "stokes16-nc3")]
+    for c, _ in out:
+        P = O.Problem(c["n"], c["n_t"], c["n_c"], c["beta"], c["reg"], c["stokes"])
+        c["mR"] = P.state(c["v_true"], c["mT"])[-1]
+    return out
+
+
+@pytest.mark.parametrize("ckpt", [2, 4])
+@pytest.mark.parametrize("quad", [0, 1])
+def test_gradient_checkpointed(ckpt_cases, ckpt, quad):
+    for c, label in ckpt_cases:
+        R, P = pair(c, ckpt=ckpt, quad=quad)
+        R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+        v = 0.5 * c["v_true"]
+        g = empty(R.coef_shape())
+        J = R.gradient(cuda(v), g)
+        go, Jo = P.gradient(v, c["mT"], c["mR"])
+        assert rel(host(g), go) < FP64_TOL, (label, ckpt, rel(host(g), go))
+        assert relmax(host(g), go) < 10 * FP64_TOL, (label, ckpt, relmax(host(g), go))
+        assert abs(J - Jo) < FP64_TOL * Jo, label
+
+
+@pytest.mark.parametrize("ckpt", [2, 4])
+@pytest.mark.parametrize("quad", [0, 1])
+def test_transport_adjoint_checkpointed(ckpt_cases, ckpt, quad):
+    for c, label in ckpt_cases:
+        R, _ = pair(c, ckpt=ckpt, quad=quad)
+        G = np.random.default_rng(3).standard_normal(c["n"])
+        gv, gm0 = empty(R.coef_shape()), empty(c["n"])
+        R.transport_adjoint(cuda(c["v_true"]), cuda(c["mT"]), cuda(G), gv, gm0)
+        Pn = O.Problem(c["n"], c["n_t"], c["n_c"], c["beta"], c["reg"], False, dto=bool(quad))
+        m1 = Pn.state(c["v_true"], c["mT"])[-1]
+        g, _ = Pn.gradient(c["v_true"], c["mT"], m1 - G)  # lambda_1 = -G
+        f = g - Pn.reg_apply(c["v_true"])
+        assert rel(host(gv), f) < FP64_TOL, (label, ckpt, rel(host(gv), f))
+        lam0 = Pn.adjoint(c["v_true"], -G)[0]
+        assert rel(host(gm0), -lam0) < FP64_TOL, (label, ckpt)
+
+
+# ---------------------------------------------------------------------------
+# Full-spectrum inputs: white-noise template, velocity and direction carry
+# every Fourier mode, the Nyquist modes included, through the packed DC /
+# Nyquist slot of the row transforms, the masked first derivatives (reading
+# R1) and the Leray projection.
+# ---------------------------------------------------------------------------
+
+def white_case(n):
+    r = np.random.default_rng(404 + sum(n))
+    if len(n) == 2:
+        c = dict(n=n, n_t=4, n_c=1, beta=1e-2, reg=2, stokes=False)
+    else:
+        c = dict(n=n, n_t=4, n_c=2, beta=1e-2, reg=1, stokes=True)
+    c["mT"] = synth.white_noise(n, r)
+    c["v_true"] = synth.white_noise_velocity(n, r, c["n_c"], 0.1)
+    c["vt"] = synth.white_noise_velocity(n, r, c["n_c"], 1.0)
+    P = O.Problem(n, c["n_t"], c["n_c"], c["beta"], c["reg"], c["stokes"])
+    c["mR"] = synth.white_noise(n, r)  # unrelated to m_T: a large adjoint everywhere
+    return c, P
+
+
+@pytest.mark.parametrize("n", [(16, 16), (8, 16, 32)], ids=["16x16", "8x16x32"])
+@pytest.mark.parametrize("precision,ckpt", [(lib.REG_FP64, 0), (lib.REG_MIXED, 0), (lib.REG_MIXED, 2)])
+def test_full_spectrum_inputs(n, precision, ckpt):
+    c, P = white_case(n)
+    tol = FP64_TOL if precision == lib.REG_FP64 else MIXED_TOL
+    R, _ = pair(c, precision=precision, ckpt=ckpt)
+    m1 = empty(n)
+    R.transport(cuda(c["v_true"]), cuda(c["mT"]), m1)
+    assert rel(host(m1), P.state(c["v_true"], c["mT"])[-1]) < FP64_TOL
+    R.set_images(cuda(c["mT"]), cuda(c["mR"]))
+    g = empty(R.coef_shape())
+    J = R.gradient(cuda(c["v_true"]), g)
+    go, Jo = P.gradient(c["v_true"], c["mT"], c["mR"])
+    assert rel(host(g), go) < FP64_TOL, rel(host(g), go)  # the gradient is FP64 in both precisions
+    assert abs(J - Jo) < FP64_TOL * Jo
+    Hv = empty(R.coef_shape())
+    R.hessvec(cuda(c["vt"]), Hv)
+    ref = P.hessvec(c["v_true"], c["mT"], c["vt"])
+    assert rel(host(Hv), ref) < tol, rel(host(Hv), ref)
+    assert relmax(host(Hv), ref) < 10 * tol, relmax(host(Hv), ref)

@@ -896,3 +896,37 @@ def test_continuation_raises_n_t_to_meet_the_cfl_target():
     assert r["n_t"] > 8
     Pn = O.Problem(c["n"], r["n_t"], 1, r["beta"], 1, False)
     assert Pn.cfl(v) <= 0.05
+
+
+# ---------------------------------------------------------------------------
+# CFL number (Sec. 3.3.1: h_t max_j max_i ||v_i(t_j)||_inf / h_x^i over the
+# time nodes t_j), against values worked out by hand
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [(16, 32), (8, 16, 32)])
+def test_cfl_of_constant_velocities_by_hand(n):
+    d, n_t = len(n), 8
+    c = np.array([0.3, -0.7, 0.45])[:d]
+    v = np.ones((1, d) + n) * c.reshape((1, d) + (1,) * d)
+    # h_t |c_i| / (2 pi / n_i), largest over the axes: 0.7 * n_1 / (2 pi n_t)
+    expect = max(abs(c[i]) * n[i] / (2 * np.pi) for i in range(d)) / n_t
+    assert abs(O.Problem(n, n_t).cfl(v) - expect) <= 1e-15 * expect
+
+
+def test_cfl_of_a_chebyshev_velocity_by_hand():
+    # v(t) = c1 + T_1(2t - 1) c2 + T_2(2t - 1) c3 with constant fields: on the
+    # nodes t = 0 and t = 1, T_1 = -1 / +1 and T_2 = 1, so the largest speed of
+    # component i is max(|c1 - c2 + c3|, |c1 + c2 + c3|) = |c1 + c3| + |c2|
+    # (the middle node t = 1/2 gives |c1 - c3|, smaller here)
+    n, n_t = (16, 8), 4
+    c1, c2, c3 = np.array([0.2, -0.1]), np.array([0.05, 0.3]), np.array([0.1, 0.02])
+    v = np.stack([np.ones((2,) + n) * c.reshape(2, 1, 1) for c in (c1, c2, c3)])
+    speed = np.abs(c1 + c3) + np.abs(c2)
+    expect = max(speed[i] * n[i] / (2 * np.pi) for i in range(2)) / n_t
+    assert abs(O.Problem(n, n_t, n_c=3).cfl(v) - expect) <= 1e-15 * expect
+    # a non-constant field: v_1 = a sin(x_2) reaches |a| on the node x_2 = pi/2
+    # (n_2 a multiple of 4), v_2 = 0
+    X = synth.coords(n)
+    a = -0.35
+    w = np.stack([a * np.sin(X[1]), np.zeros(n)])[None]
+    assert abs(O.Problem(n, n_t).cfl(w) - abs(a) * n[0] / (2 * np.pi) / n_t) <= 1e-15

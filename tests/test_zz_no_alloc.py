@@ -7,7 +7,10 @@ point works in a fixed device array instead. These checks compare it with
 reg_precond through the C ABI on two calls in a row (the second call finds
 the first call's leftovers in the shared array), check that a repeated call
 takes no device memory, and that sizes beyond the fixed capacity are
-rejected with a clear message. The file is named to run last.
+rejected with a clear message. Further cases reach the end of the array (the
+largest admissible spectra, 512-point rows, n_c = 16) and run a large, a
+small and again the large problem in a row, where stale spectra of the large
+call lie beyond the small call's extent. The file is named to run last.
 """
 import numpy as np
 import pytest
@@ -65,3 +68,49 @@ def test_sizes_beyond_the_fixed_scratch_are_rejected():
         lib.precond_noalloc(n, 1, 1e-2, lib.REG_H1, r, r)
     assert e.value.status == lib.REG_EINVAL
     assert "capacity" in str(e.value)
+
+
+def test_capacity_boundary_at_64_cubed():
+    # n_c*d*N/2 <= 2,095,040: at 64^3 (d = 3, N/2 = 131072) n_c = 5 fits and n_c = 6 does not
+    import torch
+    n = (64, 64, 64)
+    r = np.random.default_rng(21).standard_normal((5, 3) + n)
+    z = empty(r.shape)
+    lib.precond_noalloc(n, 5, 1e-2, lib.REG_H1, cuda(r), z)
+    torch.cuda.synchronize()
+    assert rel(host(z), reference(n, 5, 1e-2, lib.REG_H1, r)) < TOL
+    big = empty((6, 3) + n)
+    with pytest.raises(lib.RegError) as e:
+        lib.precond_noalloc(n, 6, 1e-2, lib.REG_H1, big, big)
+    assert e.value.status == lib.REG_EINVAL and "capacity" in str(e.value)
+
+
+def test_large_small_large_and_the_largest_tables():
+    # 512^2 with n_c = 7 (H2) fills 1,835,008 of the 2,095,040 spectral slots;
+    # 8 x 512 with n_c = 16 uses the 512-point tables and the largest Gram inverse
+    import torch
+    seq = [((512, 512), 7, 1e-3, lib.REG_H2, 31), ((16, 8, 32), 3, 3e-3, lib.REG_H2, 32),
+           ((512, 512), 7, 1e-3, lib.REG_H2, 31), ((8, 512), 16, 1e-2, lib.REG_H1, 33)]
+    outs = []
+    for n, nc, beta, reg, seed in seq:
+        r = np.random.default_rng(seed).standard_normal((nc, len(n)) + n)
+        z = empty(r.shape)
+        lib.precond_noalloc(n, nc, beta, reg, cuda(r), z)
+        torch.cuda.synchronize()
+        outs.append(host(z))
+        assert rel(outs[-1], reference(n, nc, beta, reg, r)) < TOL, (n, nc)
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_tensor_of_another_device_is_refused_without_a_launch():
+    import torch
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    n = (16, 16)
+    torch.cuda.set_device(0)
+    r1 = torch.zeros((1, 2) + n, dtype=torch.float64, device="cuda:1")
+    z0 = empty((1, 2) + n)
+    L = lib.load()
+    arr = (lib.ctypes.c_int64 * 2)(*n)
+    st = L.reg_precond_noalloc(2, arr, 1, 1e-2, lib.REG_H1, r1.data_ptr(), z0.data_ptr(), None)
+    assert st == lib.REG_EINVAL
