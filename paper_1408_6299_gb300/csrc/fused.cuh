@@ -160,7 +160,9 @@ struct RowsSpec {
   const cx<T>* p[NF];
 };
 
-enum { EPI_ADV = 1, EPI_DIV = 2, EPI_ADV2 = 3 };  // ADV2: two advection epilogues on 2 x d fields
+// ADV2: two advection epilogues on 2 x d fields; DIVS: the divergence epilogue on
+// the sum of the NF input spectra (added on load, one inverse transform)
+enum { EPI_ADV = 1, EPI_DIV = 2, EPI_ADV2 = 3, EPI_DIVS = 4 };
 
 // Hint: fetch a contiguous byte range into L2 (bulk prefetch; no completion to wait for).
 __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
@@ -392,18 +394,31 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
-  __shared__ C buf[NF * RB * RS];
+  constexpr int NX = EPI == EPI_DIVS ? 1 : NF;  // sequences transformed per row
+  __shared__ C buf[NX * RB * RS];
   const long row0 = (long)blockIdx.x * RB;
-  constexpr int PER = (NF * RB * M + kThreads - 1) / kThreads;
+  constexpr int PER = (NX * RB * M + kThreads - 1) / kThreads;
   C v[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     int e = threadIdx.x + i * kThreads;
     v[i] = mk<C>(0, 0);
-    if (e < NF * RB * M) {
+    if (e < NX * RB * M) {
       int f = e / (RB * M), rem = e % (RB * M);
       long row = row0 + rem / M;
-      if (row < nrows) v[i] = in.p[f][row * M + rem % M];
+      if (row < nrows) {
+        if constexpr (EPI == EPI_DIVS) {
+          const int j = rem % M;
+#pragma unroll
+          for (int g = 0; g < NF; ++g) {
+            C z = in.p[g][row * M + j];
+            if ((zmask >> g) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
+            v[i] = cadd(v[i], z);
+          }
+        } else {
+          v[i] = in.p[f][row * M + rem % M];
+        }
+      }
     }
   }
   // operand slices of at most 8 KB: larger blocks would prefetch more than the
@@ -420,16 +435,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     int e = threadIdx.x + i * kThreads;
-    if (e < NF * RB * M) {
+    if (e < NX * RB * M) {
       int f = e / (RB * M), rem = e % (RB * M);
       int j = rem % M;
       C z = v[i];
-      if ((zmask >> f) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
+      if (EPI != EPI_DIVS && ((zmask >> f) & 1)) z = mk<C>(-(T)j * z.y, (T)j * z.x);
       buf[(f * RB + rem / M) * RS + pad16(j)] = z;
     }
   }
   __syncthreads();
-  c2r_block<T, L, RB, NF, EPI>(buf, row0, nrows, adv, dv, tw, twrc, advB);
+  c2r_block<T, L, RB, NX, EPI>(buf, row0, nrows, adv, dv, tw, twrc, advB);
 }
 
 // Spectral derivative along a strided axis of length L on z-spectral rows:
@@ -792,6 +807,253 @@ __global__ void __launch_bounds__(TC * (R0 > L / R0 ? R0 : L / R0)) k_cols_deriv
         long o = off + (long)(j + r * Q0) * s + b;
         if (add) z = cadd(z, add[o]);
         out[o] = z;
+      }
+    }
+    // the shared-memory writes above precede, in the async proxy, the tensor
+    // copy that refills this buffer in the next iteration
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    pending_other = false;
+  }
+  // after a timeout the copies issued for this and the next tile may still be
+  // in flight: wait for them (bounded) before the block's shared memory is released
+  if (t < ntiles) {
+    (void)mbar_wait(&bar[it & 1], (it >> 1) & 1);
+    if (pending_other) (void)mbar_wait(&bar[(it & 1) ^ 1], ((it + 1) >> 1) & 1);
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Single-precision column passes of one stage in one persistent launch.
+//
+// Every thread transforms two neighbouring columns at once: a float2 holds
+// the same quantity of both columns, and the butterflies run as paired
+// single-precision instructions (add/fma/mul on float2, sm_100 and later),
+// half the arithmetic instructions of one column per thread. Between the
+// stages the tile lives in shared memory as two planes of column pairs
+// (real parts, imaginary parts), so every exchange loads ready-made pairs.
+//
+// A launch covers up to four independent column passes (jobs) of the same
+// axis length: each job has its own tensor map (input pencils), output,
+// optional add, stride and tile count, and the blocks walk the
+// concatenated tile list. One launch per stage replaces a launch per pass,
+// so the ramp-up and the partial last wave of the persistent blocks are
+// paid once per stage.
+// ---------------------------------------------------------------------------
+struct P2 {
+  float2 re, im;
+};
+__device__ __forceinline__ P2 p2_add(P2 a, P2 b) { return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)}; }
+// a - b as a + (-1) b in one fused operation per half (exact: the product by -1 is not rounded)
+__device__ __forceinline__ P2 p2_sub(P2 a, P2 b) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  return {__ffma2_rn(b.re, m1, a.re), __ffma2_rn(b.im, m1, a.im)};
+}
+// times the complex scalar (c, s), given as the duplicated pairs (c, c) and (s, s)
+__device__ __forceinline__ P2 p2_mul(P2 a, float2 cc, float2 ss) {
+  const float2 nss = __fmul2_rn(ss, make_float2(-1.f, -1.f));
+  return {__ffma2_rn(a.re, cc, __fmul2_rn(a.im, nss)), __ffma2_rn(a.re, ss, __fmul2_rn(a.im, cc))};
+}
+template <int R, int k>
+__device__ __forceinline__ P2 p2_twid(P2 o) {
+  constexpr int q = (k * 16 / R) % 16;
+  if constexpr (q == 0) return o;
+  else if constexpr (q == 4) return {o.im, make_float2(-o.re.x, -o.re.y)};  // times -i
+  else if constexpr (q == 8) return {make_float2(-o.re.x, -o.re.y), make_float2(-o.im.x, -o.im.y)};
+  else if constexpr (q == 12) return {make_float2(-o.im.x, -o.im.y), o.re};  // times i
+  else {
+    const float2 w = root16<float, q>();
+    return p2_mul(o, make_float2(w.x, w.x), make_float2(w.y, w.y));
+  }
+}
+// forward DFT of size R on paired values (radix-2 decimation in time, as Dft)
+template <int R>
+struct P2Dft {
+  template <int k>
+  static __device__ __forceinline__ void comb(P2* v, const P2* e, const P2* o) {
+    if constexpr (k < R / 2) {
+      const P2 t = p2_twid<R, k>(o[k]);
+      v[k] = p2_add(e[k], t);
+      v[k + R / 2] = p2_sub(e[k], t);
+      comb<k + 1>(v, e, o);
+    }
+  }
+  static __device__ __forceinline__ void run(P2* v) {
+    P2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    P2Dft<R / 2>::run(e);
+    P2Dft<R / 2>::run(o);
+    comb<0>(v, e, o);
+  }
+};
+template <>
+struct P2Dft<1> {
+  static __device__ __forceinline__ void run(P2*) {}
+};
+
+// float2 slot of (row, column pair cp) in one plane of 8 pairs per row; the
+// rows of every odd 16-row group swap places pairwise, so the rows 16a + b
+// that one store instruction touches fall on alternating halves of the banks
+__device__ __forceinline__ int plane_slot(int row, int cp) { return ((row ^ ((row >> 4) & 1)) << 3) + cp; }
+
+constexpr int kColJobs = 4;
+struct ColJobs {
+  float2* out[kColJobs];
+  const float2* add[kColJobs];  // null: no add
+  long s[kColJobs];             // stride between pencil elements (complex values)
+  int ntx[kColJobs];            // tiles across the inner extent s / 16
+  int start[kColJobs + 1];      // first global tile of each job; start[nj] = all tiles
+  int nj;
+};
+
+// out = IFFT_a(i k~_a FFT_a(in)) (+ add) for the jobs' pencils of length
+// L = R0 * R1, tiles of 16 columns, 8 column pairs x max(L/R0, R0) threads.
+// Stages: A (radix R0) from the TMA tile, B (radix R1) with twiddles
+// W_L^{r j}, the multiplier, the inverse first stage A' (radix R1) on the
+// same registers, and B' (radix R0, twiddles read transposed) to global
+// memory, as in k_cols_deriv2. tw2: the stage-1 twiddle block of length L
+// with each entry (c, s) stored as (c, c, s, s).
+template <int L, int R0, int R1>
+__global__ void __launch_bounds__(8 * (L / R0 > R0 ? L / R0 : R0)) k_cols_pairs(
+    const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
+    const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap m3, ColJobs J,
+    const float4* __restrict__ tw2) {
+  constexpr int TC = 16;
+  constexpr int Q0 = L / R0, Q1 = R0;
+  constexpr unsigned TILE_BYTES = L * TC * sizeof(float2);
+  constexpr int XW = TC * 2;  // box width in 4-byte elements
+  constexpr int RMAX = R0 > R1 ? R0 : R1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  float2* bufs = reinterpret_cast<float2*>(smem_raw);  // two tiles of L x TC complex values
+  const int cp = threadIdx.x & 7, j = threadIdx.x >> 3;
+  const int ntiles = J.start[J.nj];
+  auto job_of = [&](int tt) {
+    int q = 0;
+#pragma unroll
+    for (int k = 1; k < kColJobs; ++k)
+      if (k < J.nj && tt >= J.start[k]) q = k;
+    return q;
+  };
+  auto issue = [&](int tt, int b) {  // one thread
+    const int q = job_of(tt);
+    const int lt = tt - J.start[q];
+    const CUtensorMap* mp = q == 0 ? &m0 : (q == 1 ? &m1 : (q == 2 ? &m2 : &m3));
+    mbar_expect_tx(&bar[b], TILE_BYTES);
+    tma_load_2d(bufs + b * L * TC, mp, (lt % J.ntx[q]) * XW, (lt / J.ntx[q]) * L, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  int t = blockIdx.x;
+  if (threadIdx.x == 0 && t < ntiles) issue(t, 0);
+  int it = 0;
+  bool pending_other = false;  // a copy into the other buffer is in flight
+  const float sc = 1.f / (float)L;
+  P2 v[RMAX];
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int cb = it & 1;
+    float2* cur = bufs + cb * L * TC;
+    float2* pre = cur;               // plane of real parts
+    float2* pim = cur + L * TC / 2;  // plane of imaginary parts
+    const int q = job_of(t);
+    const int lt = t - J.start[q];
+    const long s = J.s[q];
+    const long off = (long)(lt / J.ntx[q]) * L * s + (long)(lt % J.ntx[q]) * TC;
+    const int tn = t + gridDim.x;
+    pending_other = tn < ntiles;
+    if (threadIdx.x == 0 && pending_other) issue(tn, cb ^ 1);
+    // all threads agree on the outcome, so a timeout ends the whole block together
+    if (!__syncthreads_and(mbar_wait(&bar[cb], (it >> 1) & 1))) {
+      if (threadIdx.x == 0) atomicAdd(&g_tma_timeouts, 1);
+      break;
+    }
+    // forward stage A from the tile (complex values of columns 2cp, 2cp+1 are one float4)
+    if (j < Q0) {
+      const float4* c4 = reinterpret_cast<const float4*>(cur);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const float4 x = c4[(j + r * Q0) * (TC / 2) + cp];
+        v[r].re = make_float2(x.x, x.z);
+        v[r].im = make_float2(x.y, x.w);
+      }
+      P2Dft<R0>::run(v);
+    }
+    __syncthreads();  // the tile has been read: its buffer now holds the planes
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        pre[plane_slot(j * R0 + r, cp)] = v[r].re;
+        pim[plane_slot(j * R0 + r, cp)] = v[r].im;
+      }
+    }
+    __syncthreads();
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        v[r].re = pre[plane_slot(j + r * R0, cp)];
+        v[r].im = pim[plane_slot(j + r * R0, cp)];
+      }
+#pragma unroll
+      for (int r = 1; r < R1; ++r) {
+        const float4 w = __ldg(&tw2[r * R0 + j]);
+        v[r] = p2_mul(v[r], make_float2(w.x, w.y), make_float2(w.z, w.w));
+      }
+      P2Dft<R1>::run(v);
+      // v[r] is frequency j + r*R0: conj(i k~ z / L) = (-k z.im, -k z.re) with k = k~ / L
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const float k = kmask_f<float, L>((float)(j + r * R0)) * sc;
+        const float2 nk = make_float2(-k, -k);
+        const float2 re = __fmul2_rn(v[r].im, nk);
+        v[r].im = __fmul2_rn(v[r].re, nk);
+        v[r].re = re;
+      }
+      P2Dft<R1>::run(v);  // inverse stage A' on the same values
+    }
+    __syncthreads();  // every thread has read the planes of stage B
+    if (j < Q1) {
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        pre[plane_slot(j * R1 + r, cp)] = v[r].re;
+        pim[plane_slot(j * R1 + r, cp)] = v[r].im;
+      }
+    }
+    __syncthreads();
+    if (j < Q0) {
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        v[r].re = pre[plane_slot(j + r * Q0, cp)];
+        v[r].im = pim[plane_slot(j + r * Q0, cp)];
+      }
+#pragma unroll
+      for (int r = 1; r < R0; ++r) {
+        const float4 w = __ldg(&tw2[j * R0 + r]);
+        v[r] = p2_mul(v[r], make_float2(w.x, w.y), make_float2(w.z, w.w));
+      }
+      P2Dft<R0>::run(v);
+      float2* out = J.out[q];
+      const float2* add = J.add[q];
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        float4 z = make_float4(v[r].re.x, -v[r].im.x, v[r].re.y, -v[r].im.y);  // conjugated back
+        const long o = off + (long)(j + r * Q0) * s + 2 * cp;
+        if (add) {
+          const float4 a = *reinterpret_cast<const float4*>(add + o);
+          z.x += a.x;
+          z.y += a.y;
+          z.z += a.z;
+          z.w += a.w;
+        }
+        *reinterpret_cast<float4*>(out + o) = z;
       }
     }
     // the shared-memory writes above precede, in the async proxy, the tensor

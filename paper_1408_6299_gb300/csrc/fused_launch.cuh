@@ -58,10 +58,11 @@ void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, 
   // 1024 for more (4 and 8 rows at L = 256), so that the epilogue operand
   // slices stay within the prefetch limit (measured on the 256^3 matvec:
   // 298 -> 290 ms against the element-count rule of the other passes)
-  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NF == 1 || NF > 4 ? 8 : 4) * M)
-                                     : row_elems<T>() / ((NF > 4 ? 8 : pow2_ceil(NF)) * M);
+  constexpr int NX = EPI == EPI_DIVS ? 1 : NF;  // sequences transformed per row
+  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NX == 1 || NX > 4 ? 8 : 4) * M)
+                                     : row_elems<T>() / ((NX > 4 ? 8 : pow2_ceil(NX)) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
-  ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * NF * (fft_flops<M>() + 8.0 * M));
+  ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * NX * (fft_flops<M>() + 8.0 * M));
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
   k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc, advB);
   REG_LAUNCH();
@@ -318,6 +319,98 @@ void deriv(const Grid& g, const Spectral<T>& sp, int axis, const cx<T>* in, cx<T
   throw StatusError{1, "unsupported axis length"};
 }
 
+// pencil geometry of a strided pass along `axis` of the z-spectral rows:
+// element j of pencil (outer, inner) at outer*n*s + j*s + inner
+inline void col_geometry(const Grid& g, int axis, long* s, long* outer) {
+  long st = g.M;
+  for (int a = axis + 1; a < g.d - 1; ++a) st *= g.n[a];
+  *s = st;
+  *outer = g.Nc / (st * g.n[axis]);
+}
+
+// One strided derivative pass of a stage: out = D_axis in (+ add)
+template <typename T>
+struct ColJob {
+  int axis;
+  const cx<T>* in;
+  cx<T>* out;
+  const cx<T>* add;
+};
+
+template <int L>
+void cols_pairs_L(const Spectral<float>& sp, const Grid& g, const ColJob<float>* jobs, int nj, cudaStream_t st) {
+  constexpr int R0 = Plan<L>::R[0], R1 = Plan<L>::R[1];
+  constexpr int NT = 8 * (L / R0 > R0 ? L / R0 : R0);
+  constexpr size_t smem = 2 * (size_t)L * 16 * sizeof(float2);
+  CUtensorMap maps[kColJobs];
+  ColJobs J{};
+  J.nj = nj;
+  double bytes = 0, flops = 0;
+  int acc = 0;
+  for (int q = 0; q < nj; ++q) {
+    long s, outer;
+    col_geometry(g, jobs[q].axis, &s, &outer);
+    if (!cols_tensor_map<float, L, 16>(&maps[q], jobs[q].in, s, outer))
+      throw StatusError{3, "column pass: tensor map rejected"};
+    J.out[q] = jobs[q].out;
+    J.add[q] = jobs[q].add;
+    J.s[q] = s;
+    J.ntx[q] = (int)(s / 16);
+    J.start[q] = acc;
+    acc += (int)(s / 16 * outer);
+    bytes += (double)s * outer * L * sizeof(float2) * (jobs[q].add ? 3.0 : 2.0);
+    flops += (double)s * outer * (2.0 * fft_flops<L>() + L * (jobs[q].add ? 4.0 : 2.0));
+  }
+  for (int q = nj; q < kColJobs; ++q) maps[q] = maps[0];
+  J.start[nj] = acc;
+  ProfScope ps(KK_COLS, st, bytes, flops);
+  // resident blocks of one wave, computed once (thread-safe static initialisation)
+  static const int resident = persistent_wave(k_cols_pairs<L, R0, R1>, NT, smem);
+  const int grid = acc < resident ? acc : resident;
+  k_cols_pairs<L, R0, R1><<<grid, NT, smem, st>>>(maps[0], maps[1], maps[2], maps[3], J, sp.pair_twiddles(L));
+  REG_LAUNCH();
+}
+
+// The strided passes of one stage in as few launches as possible: with single
+// precision, two-stage radix plans and fields that stream through DRAM (the
+// persistent regime, more than 16 MB per field), all jobs of one axis length
+// share one launch of k_cols_pairs. Returns false without launching anything
+// when some job does not qualify; the caller then runs deriv() per job.
+template <typename T>
+bool cols_pairs(const Spectral<T>& sp, const ColJob<T>* jobs, int nj, cudaStream_t st) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    const Grid& g = sp.grid();
+    const char* env = getenv("REG_PAIRED_COLS");
+    if (env && env[0] == '0') return false;
+    for (int q = 0; q < nj; ++q) {
+      const int L = g.n[jobs[q].axis];
+      long s, outer;
+      col_geometry(g, jobs[q].axis, &s, &outer);
+      if (L < 32 || L > 256 || s % 16 || (size_t)s * outer * L * sizeof(float2) <= (16ull << 20) ||
+          ((uintptr_t)jobs[q].in & 15) || ((uintptr_t)jobs[q].out & 15) || ((uintptr_t)jobs[q].add & 15) ||
+          !sp.pair_twiddles(L))
+        return false;
+    }
+    // one launch per distinct axis length, jobs in their given order
+    for (int done = 0; done < nj;) {
+      const int L = g.n[jobs[done].axis];
+      ColJob<float> grp[kColJobs];
+      int m = 0;
+      for (int q = done; q < nj && g.n[jobs[q].axis] == L; ++q) grp[m++] = jobs[q];
+      switch (L) {
+        case 32: cols_pairs_L<32>(sp, g, grp, m, st); break;
+        case 64: cols_pairs_L<64>(sp, g, grp, m, st); break;
+        case 128: cols_pairs_L<128>(sp, g, grp, m, st); break;
+        default: cols_pairs_L<256>(sp, g, grp, m, st); break;
+      }
+      done += m;
+    }
+    return true;
+  }
+}
+
 template <typename T>
 void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy) {
   const Grid& g = sp.grid();
@@ -333,15 +426,18 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
                   (e.out1 ? d + (e.src ? 1 : (e.gm[0] ? 2 * d : 0)) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1) : 0));
   DivEpi<T> none{};
   if (d == 3) {
-    // the two strided passes are independent: the x pass runs on the second
-    // stream, so each fills the other's last partial wave of blocks
-    cudaStream_t s2 = sp.aux_stream();
-    REG_CUDA(cudaEventRecord(sp.fork_event(), s));
-    REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
-    deriv<T>(g, sp, 0, U, Zx, nullptr, s2);
-    deriv<T>(g, sp, 1, U, Zy, nullptr, s);
-    REG_CUDA(cudaEventRecord(sp.join_event(), s2));
-    REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
+    const ColJob<T> jobs[2] = {{0, U, Zx, nullptr}, {1, U, Zy, nullptr}};
+    if (!cols_pairs<T>(sp, jobs, 2, s)) {
+      // the two strided passes are independent: the x pass runs on the second
+      // stream, so each fills the other's last partial wave of blocks
+      cudaStream_t s2 = sp.aux_stream();
+      REG_CUDA(cudaEventRecord(sp.fork_event(), s));
+      REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
+      deriv<T>(g, sp, 0, U, Zx, nullptr, s2);
+      deriv<T>(g, sp, 1, U, Zy, nullptr, s);
+      REG_CUDA(cudaEventRecord(sp.join_event(), s2));
+      REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
+    }
     RowsSpec<T, 3> in{{Zx, Zy, U}};
     c2r<T, 3, EPI_ADV>(g, s, in, 1 << 2, e, none, bytes, tw, twrc);
   } else {
@@ -377,15 +473,18 @@ void adv2_stage_impl(Spectral<T>& sp, const T* uA, const AdvEpi<T>& eA, const T*
                           (e.stage == 1 ? 2 : 1)
                     : 0));
   };
-  cudaStream_t s2 = sp.aux_stream();
-  REG_CUDA(cudaEventRecord(sp.fork_event(), s));
-  REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
-  deriv<T>(g, sp, 0, UA, XA, nullptr, s2);
-  deriv<T>(g, sp, 0, UB, XB, nullptr, s2);
-  deriv<T>(g, sp, 1, UA, YA, nullptr, s);
-  deriv<T>(g, sp, 1, UB, YB, nullptr, s);
-  REG_CUDA(cudaEventRecord(sp.join_event(), s2));
-  REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
+  const ColJob<T> jobs[4] = {{0, UA, XA, nullptr}, {0, UB, XB, nullptr}, {1, UA, YA, nullptr}, {1, UB, YB, nullptr}};
+  if (!cols_pairs<T>(sp, jobs, 4, s)) {
+    cudaStream_t s2 = sp.aux_stream();
+    REG_CUDA(cudaEventRecord(sp.fork_event(), s));
+    REG_CUDA(cudaStreamWaitEvent(s2, sp.fork_event(), 0));
+    deriv<T>(g, sp, 0, UA, XA, nullptr, s2);
+    deriv<T>(g, sp, 0, UB, XB, nullptr, s2);
+    deriv<T>(g, sp, 1, UA, YA, nullptr, s);
+    deriv<T>(g, sp, 1, UB, YB, nullptr, s);
+    REG_CUDA(cudaEventRecord(sp.join_event(), s2));
+    REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
+  }
   DivEpi<T> none{};
   RowsSpec<T, 6> in6{{XA, YA, UA, XB, YB, UB}};
   // a velocity read by both epilogues (the same node, or n_c = 1) is counted once
@@ -411,10 +510,18 @@ void div_stage_impl(Spectral<T>& sp, const T* lam, const T* a, const DivEpi<T>& 
     RowsIn<T, 3> in{{a, a + N, a + 2 * N}};
     RowsOut<T, 3> out{{Q0, Q1, Q2}};
     r2c<T, 3, true>(g, s, in, lam, out, 1 << 2, tw, twrc);
-    deriv<T>(g, sp, 1, Q1, Q2, Q2, s);
-    deriv<T>(g, sp, 0, Q0, Q2, Q2, s);
-    RowsSpec<T, 1> sp1{{Q2}};
-    c2r<T, 1, EPI_DIV>(g, s, sp1, 0, none, e, bytes, tw, twrc);
+    // the two strided derivatives in place, independent of each other (one
+    // launch); the row pass adds the three spectra on load
+    const ColJob<T> jobs[2] = {{0, Q0, Q0, nullptr}, {1, Q1, Q1, nullptr}};
+    if (cols_pairs<T>(sp, jobs, 2, s)) {
+      RowsSpec<T, 3> sp3{{Q0, Q1, Q2}};
+      c2r<T, 3, EPI_DIVS>(g, s, sp3, 0, none, e, bytes + 2.0 * N * sizeof(T), tw, twrc);
+    } else {
+      deriv<T>(g, sp, 1, Q1, Q2, Q2, s);
+      deriv<T>(g, sp, 0, Q0, Q2, Q2, s);
+      RowsSpec<T, 1> sp1{{Q2}};
+      c2r<T, 1, EPI_DIV>(g, s, sp1, 0, none, e, bytes, tw, twrc);
+    }
   } else {
     RowsIn<T, 2> in{{a, a + N}};
     RowsOut<T, 2> out{{Q0, Q1}};

@@ -140,6 +140,10 @@ class Spectral {
 
   const C* twiddles(int L) const;   // Stockham stage tables for length L
   const C* rc_twiddles() const;     // exp(-2 pi i k / L_last), k < M
+  // single precision, two-stage plans (L = 32..256): the stage-1 twiddle
+  // block of length L with each entry (c, s) stored as (c, c, s, s), for the
+  // paired column passes; null otherwise
+  const float4* pair_twiddles(int L) const;
 
   // A second stream with a fork and a join event, for independent passes of
   // one stage (created on first use).
@@ -154,6 +158,8 @@ class Spectral {
   cudaStream_t aux_ = nullptr;
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   C* tw_ = nullptr;  // device: tables per length + real/complex table
+  float4* tw2_ = nullptr;  // device: paired twiddle blocks (single precision only)
+  long tw2_off_[11] = {0};
   bool owns_ = true;
   long tw_off_[11] = {0};  // offset of the table of length 2^e
   long rc_off_ = 0;

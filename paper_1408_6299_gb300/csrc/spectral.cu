@@ -498,6 +498,18 @@ Spectral<T>::Spectral(const Grid& g, cudaStream_t s) : g_(g), s_(s) {
   for (size_t i = 0; i < all.size(); ++i) h[i] = (T)all[i];
   REG_CUDA(cudaMalloc(&tw_, h.size() * sizeof(T)));
   REG_CUDA(cudaMemcpy(tw_, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (sizeof(T) == 4) {
+    // the two-stage plans' stage-1 blocks (L = 32..256) with duplicated entries
+    std::vector<float4> p2;
+    for (int e = 5; e <= 8; ++e) {
+      tw2_off_[e] = (long)p2.size();
+      std::vector<double> t = stage_table(1 << e);
+      for (size_t i = 0; i + 1 < t.size(); i += 2)
+        p2.push_back(make_float4((float)t[i], (float)t[i], (float)t[i + 1], (float)t[i + 1]));
+    }
+    REG_CUDA(cudaMalloc(&tw2_, p2.size() * sizeof(float4)));
+    REG_CUDA(cudaMemcpy(tw2_, p2.data(), p2.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  }
 }
 
 template <typename T>
@@ -552,6 +564,7 @@ long Spectral<T>::write_tables(double* out, long* tw_off, long* rc_off) {
 template <typename T>
 Spectral<T>::~Spectral() {
   if (tw_ && owns_) cudaFree(tw_);
+  if (tw2_ && owns_) cudaFree(tw2_);
   if (ev_fork_) cudaEventDestroy(ev_fork_);
   if (ev_join_) cudaEventDestroy(ev_join_);
   if (aux_) cudaStreamDestroy(aux_);
@@ -574,6 +587,11 @@ const cx<T>* Spectral<T>::twiddles(int L) const {
 template <typename T>
 const cx<T>* Spectral<T>::rc_twiddles() const {
   return tw_ + rc_off_;
+}
+template <typename T>
+const float4* Spectral<T>::pair_twiddles(int L) const {
+  if (!tw2_ || L < 32 || L > 256) return nullptr;
+  return tw2_ + tw2_off_[ilog2(L)];
 }
 
 template <typename T>

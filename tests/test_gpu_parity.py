@@ -306,3 +306,34 @@ def test_full_spectrum_inputs(n, precision, ckpt):
     ref = P.hessvec(c["v_true"], c["mT"], c["vt"])
     assert rel(host(Hv), ref) < tol, rel(host(Hv), ref)
     assert relmax(host(Hv), ref) < 10 * tol, relmax(host(Hv), ref)
+
+
+# ---------------------------------------------------------------------------
+# Large single-precision fields (over 16 MB per spectrum) take the paired
+# column kernel: all strided passes of a stage in one persistent launch. The
+# second shape has different x and y lengths (128 and 256): one launch per
+# length. n_t = 2 and a slow velocity keep Heun's amplification of the top
+# modes small (CFL <= 0.41).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [(256, 256, 128), (128, 256, 256)], ids=["256x256x128", "128x256x256"])
+def test_mixed_matvec_with_paired_column_passes(n):
+    r = np.random.default_rng(606)
+    mT = synth.random_spectral_field(n, r, 24.0)
+    mT /= mT.std()
+    v = np.stack([synth.velocity_field(n, r, 4, 0.02)])
+    vt = np.stack([synth.velocity_field(n, r, 4, 1.0)])
+    c = dict(n=n, n_t=2, n_c=1, beta=1e-3, reg=2, stokes=False)
+    P = O.Problem(n, 2, 1, 1e-3, 2, False)
+    mR = P.state(v, mT)[-1]
+    ref = P.hessvec(v, mT, vt)
+    for ckpt in (0, 2):
+        R, _ = pair(c, precision=lib.REG_MIXED, ckpt=ckpt)
+        R.set_images(cuda(mT), cuda(mR))
+        R.linearize(cuda(v))
+        Hv = empty(R.coef_shape())
+        R.hessvec(cuda(vt), Hv)
+        err = rel(host(Hv), ref)
+        assert err < MIXED_TOL, (ckpt, err)
+        assert relmax(host(Hv), ref) < 10 * MIXED_TOL, ckpt
+        R.close()
