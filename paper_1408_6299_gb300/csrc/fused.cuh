@@ -40,6 +40,46 @@ struct RowsOut {
   cx<T>* p[NF];
 };
 
+// Packing step of the real-to-complex rows: buf holds, for NF x RB rows, the
+// forward FFT of length M = L/2 of each row read as M complex values
+// (x_{2j} + i x_{2j+1}); it writes the packed half spectrum of every row
+// (slot 0 carries the DC and Nyquist values as re and im) to out[f]. Fields
+// whose bit is set in zmask leave multiplied by i k_last (slot 0 -> 0).
+template <typename T, int L, int RB, int NF>
+__device__ __forceinline__ void r2c_pack(const cx<T>* buf, long row0, long nrows, cx<T>* const* out, int zmask,
+                                         const cx<T>* __restrict__ twrc) {
+  using C = cx<T>;
+  constexpr int M = L / 2;
+  constexpr int RS = padded_len(M);
+  constexpr int H = M / 2 + 1;
+  for (int e = threadIdx.x; e < NF * RB * H; e += kThreads) {
+    int seq = e / H, k = e % H;
+    int f = seq / RB, r = seq % RB;
+    long row = row0 + r;
+    if (row >= nrows) continue;
+    C* o = out[f] + row * M;
+    const C* b = buf + seq * RS;
+    bool dz = (zmask >> f) & 1;
+    if (k == 0) {
+      C z0 = b[0];
+      o[0] = dz ? mk<C>(0, 0) : mk<C>(z0.x + z0.y, z0.x - z0.y);
+    } else {
+      C zk = b[pad16(k)], zm = b[pad16(M - k)];
+      C E = cscale(cadd(zk, cconj(zm)), (T)0.5);
+      C Od = cscale(cmul_mi(csub(zk, cconj(zm))), (T)0.5);
+      C t = cmul(__ldg(&twrc[k]), Od);
+      C xk = cadd(E, t);
+      C xm = cconj(csub(E, t));
+      if (dz) {  // times i k
+        xk = mk<C>(-(T)k * xk.y, (T)k * xk.x);
+        xm = mk<C>(-(T)(M - k) * xm.y, (T)(M - k) * xm.x);
+      }
+      o[k] = xk;
+      if (k != M - k) o[M - k] = xm;
+    }
+  }
+}
+
 // Real-to-complex rows of NF fields in one block. PROD: field f is a_f * lam
 // (pointwise), else in_f. Fields whose bit is set in zmask leave multiplied by
 // i k_last (first derivative along the last axis; slot 0 -> 0).
@@ -81,33 +121,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_r2c_n(RowsIn<T, NF> in, const
   }
   __syncthreads();
   smem_fft<T, M, false, kThreads, NF * RB>(buf, RS, tw);
-  constexpr int H = M / 2 + 1;
-  for (int e = threadIdx.x; e < NF * RB * H; e += kThreads) {
-    int seq = e / H, k = e % H;
-    int f = seq / RB, r = seq % RB;
-    long row = row0 + r;
-    if (row >= nrows) continue;
-    C* o = out.p[f] + row * M;
-    const C* b = buf + seq * RS;
-    bool dz = (zmask >> f) & 1;
-    if (k == 0) {
-      C z0 = b[0];
-      o[0] = dz ? mk<C>(0, 0) : mk<C>(z0.x + z0.y, z0.x - z0.y);
-    } else {
-      C zk = b[pad16(k)], zm = b[pad16(M - k)];
-      C E = cscale(cadd(zk, cconj(zm)), (T)0.5);
-      C Od = cscale(cmul_mi(csub(zk, cconj(zm))), (T)0.5);
-      C t = cmul(__ldg(&twrc[k]), Od);
-      C xk = cadd(E, t);
-      C xm = cconj(csub(E, t));
-      if (dz) {  // times i k
-        xk = mk<C>(-(T)k * xk.y, (T)k * xk.x);
-        xm = mk<C>(-(T)(M - k) * xm.y, (T)(M - k) * xm.x);
-      }
-      o[k] = xk;
-      if (k != M - k) o[M - k] = xm;
-    }
-  }
+  r2c_pack<T, L, RB, NF>(buf, row0, nrows, out.p, zmask, twrc);
 }
 
 // Epilogue parameters of the advection stage (state / incremental state).
@@ -126,6 +140,7 @@ struct AdvEpi {
   T h;
   int stage;
   int src_from_a;  // two-field stage, second field: the source is the first field's Sout value
+  int out1_spectral_only;  // out1 is only passed on as a spectrum (the row pass emits it): no real store
 };
 
 // Epilogue parameters of the divergence stage (adjoint / incremental adjoint).
@@ -153,6 +168,16 @@ struct DivEpi {
   const T* src;     // added to the divergence
   const T* gmC;     // d fields or null
   const T* yC;
+};
+
+// The spectrum a one-field advection stage's complex-to-real pass emits for
+// the next stage, so that stage needs no real-to-complex pass: the forward
+// row transform of the stage's out1 values. out[0] receives the packed half
+// spectrum of the rows the block itself read (row-local, so it may overwrite
+// the pass's own input spectrum).
+template <typename T>
+struct Emit {
+  cx<T>* out[1];
 };
 
 template <typename T, int NF>
@@ -210,7 +235,8 @@ __device__ __forceinline__ void prefetch_epilogue(const AdvEpi<T>& adv, const Di
 // (-a.g [- source], Heun update, optional keep of g or of g.sw). srcv, when
 // given, is the source value instead of e.src. Returns the Sout value.
 template <typename T, int D>
-__device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, long q, const cx<T>* srcv) {
+__device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, long q, const cx<T>* srcv,
+                                           cx<T>* o1 = nullptr) {
   using C = cx<T>;
   C so = mk<C>(0, 0);
   if (e.G[0]) {
@@ -252,25 +278,33 @@ __device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, l
       k1 -= gm.y * w.y;
     }
   }
+  C r1;
   if (e.stage == 1) {
     C yv = e.y ? reinterpret_cast<const C*>(e.y)[q] : mk<C>(0, 0);
-    reinterpret_cast<C*>(e.out1)[q] = mk<C>(yv.x + e.h * k0, yv.y + e.h * k1);
+    r1 = mk<C>(yv.x + e.h * k0, yv.y + e.h * k1);
     reinterpret_cast<C*>(e.out2)[q] = mk<C>(yv.x + (T)0.5 * e.h * k0, yv.y + (T)0.5 * e.h * k1);
   } else {
     C yv = reinterpret_cast<const C*>(e.y)[q];
-    reinterpret_cast<C*>(e.out1)[q] = mk<C>(yv.x + (T)0.5 * e.h * k0, yv.y + (T)0.5 * e.h * k1);
+    r1 = mk<C>(yv.x + (T)0.5 * e.h * k0, yv.y + (T)0.5 * e.h * k1);
   }
+  if (!e.out1_spectral_only) reinterpret_cast<C*>(e.out1)[q] = r1;
+  if (o1) *o1 = r1;
   return so;
 }
 
 // Inverse row transforms of one staged row block (NF fields x RB rows of
 // packed spectra in buf, padded rows of RS) and the stage epilogue of rows
 // row0..row0+RB-1. Called by all threads of the block after buf is complete.
-template <typename T, int L, int RB, int NF, int EPI>
+// NE = 1 (advection only): the block then transforms the epilogue's out1
+// values forward in the same buffer and writes their packed spectrum to
+// em.out[0].
+template <typename T, int L, int RB, int NF, int EPI, int NE>
 __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
                                           const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
-                                          const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB) {
+                                          const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB,
+                                          const Emit<T>& em) {
   using C = cx<T>;
+  static_assert(NE == 0 || (NE == 1 && EPI == EPI_ADV), "only one-field advection stages emit a spectrum");
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
   constexpr int H = M / 2 + 1;
@@ -293,7 +327,15 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
   __syncthreads();
   smem_fft<T, M, false, kThreads, NF * RB>(buf, RS, tw);
   const T s = (T)1 / (T)M;
-  for (int e = threadIdx.x; e < RB * M; e += kThreads) {
+  constexpr int ITER = (RB * M + kThreads - 1) / kThreads;
+  constexpr int NEA = NE > 0 ? NE : 1;
+  C ev[ITER][NEA];  // emitted values (point pairs) of this thread
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int e = threadIdx.x + it * kThreads;
+#pragma unroll
+    for (int f = 0; f < NEA; ++f) ev[it][f] = mk<C>(0, 0);
+    if (e >= RB * M) continue;
     int r = e / M, j = e % M;
     long row = row0 + r;
     if (row >= nrows) continue;
@@ -305,7 +347,7 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
       g[f] = mk<C>(z.x * s, -z.y * s);
     }
     if (EPI == EPI_ADV) {
-      adv_point<T, NF>(adv, g, q, nullptr);
+      adv_point<T, NF>(adv, g, q, nullptr, &ev[it][0]);
     } else if (EPI == EPI_ADV2) {
       const C sa = adv_point<T, NF / 2>(adv, g, q, nullptr);
       adv_point<T, NF / 2>(advB, g + NF / 2, q, advB.src_from_a ? &sa : nullptr);
@@ -347,13 +389,13 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
           }
           for (int l = 0; l < dv.nc; ++l) {
             C hi[3], lo[3];
-            C* H = reinterpret_cast<C*>(dv.f_hi + (long)l * dv.d * dv.N);
+            C* Hf = reinterpret_cast<C*>(dv.f_hi + (long)l * dv.d * dv.N);
             C* Lo = dv.f_lo ? reinterpret_cast<C*>(dv.f_lo + (long)l * dv.d * dv.N) : nullptr;
             const long hN = dv.N / 2;
 #pragma unroll
             for (int i = 0; i < 3; ++i)
               if (i < dv.d) {
-                hi[i] = H[i * hN + q];
+                hi[i] = Hf[i * hN + q];
                 lo[i] = Lo ? Lo[i * hN + q] : mk<C>(0, 0);
               }
 #pragma unroll
@@ -366,10 +408,10 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
                   T s0 = h.x + t0, b0 = s0 - h.x, s1 = h.y + t1, b1 = s1 - h.y;
                   lo[i].x += (h.x - (s0 - b0)) + (t0 - b0);
                   lo[i].y += (h.y - (s1 - b1)) + (t1 - b1);
-                  H[i * hN + q] = mk<C>(s0, s1);
+                  Hf[i * hN + q] = mk<C>(s0, s1);
                   Lo[i * hN + q] = lo[i];
                 } else {
-                  H[i * hN + q] = mk<C>(hi[i].x + t0, hi[i].y + t1);
+                  Hf[i * hN + q] = mk<C>(hi[i].x + t0, hi[i].y + t1);
                 }
               }
           }
@@ -379,23 +421,42 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
       }
     }
   }
+  if constexpr (NE > 0) {
+    // the forward row transform of the emitted values, as the r2c pass does it
+    __syncthreads();  // every thread has read the inverse transforms from buf
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+      const int e = threadIdx.x + it * kThreads;
+      if (e < RB * M) {
+#pragma unroll
+        for (int f = 0; f < NE; ++f) buf[(f * RB + e / M) * RS + pad16(e % M)] = ev[it][f];
+      }
+    }
+    __syncthreads();
+    smem_fft<T, M, false, kThreads, NE * RB>(buf, RS, tw);
+    r2c_pack<T, L, RB, NE>(buf, row0, nrows, em.out, 0, twrc);
+  }
 }
 
 
 // Complex-to-real rows of NF fields, then the stage epilogue on the real
 // values (each thread handles a pair of neighbouring points). Fields whose
 // bit is set in zmask are multiplied by i k_last on load.
-template <typename T, int L, int RB, int NF, int EPI>
+template <typename T, int L, int RB, int NF, int EPI, int NE>
 // single precision: at most 40 registers, six resident blocks per SM. Measured on the 256^3 matvec:
-// 285.0 -> 280.5 ms against five; the divergence epilogue spills a few words and still gains.
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n(RowsSpec<T, NF> in, int zmask, AdvEpi<T> adv,
+// 285.0 -> 280.5 ms against five; the divergence epilogue spills a few words and still gains. The
+// variant that also emits the next stage's spectrum runs five blocks (measured better than six,
+// four and three).
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NE > 0 ? 5 : 6) : 1) k_rows_c2r_n(RowsSpec<T, NF> in, int zmask, AdvEpi<T> adv,
                                                           DivEpi<T> dv, long nrows, const cx<T>* __restrict__ tw,
-                                                          const cx<T>* __restrict__ twrc, AdvEpi<T> advB) {
+                                                          const cx<T>* __restrict__ twrc, AdvEpi<T> advB,
+                                                          Emit<T> em) {
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
   constexpr int NX = EPI == EPI_DIVS ? 1 : NF;  // sequences transformed per row
-  __shared__ C buf[NX * RB * RS];
+  constexpr int NB = NX > NE ? NX : NE;         // sequences the buffer holds
+  __shared__ C buf[NB * RB * RS];
   const long row0 = (long)blockIdx.x * RB;
   constexpr int PER = (NX * RB * M + kThreads - 1) / kThreads;
   C v[PER];
@@ -444,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) k_rows_c2r_n
     }
   }
   __syncthreads();
-  c2r_block<T, L, RB, NX, EPI>(buf, row0, nrows, adv, dv, tw, twrc, advB);
+  c2r_block<T, L, RB, NX, EPI, NE>(buf, row0, nrows, adv, dv, tw, twrc, advB, em);
 }
 
 // Spectral derivative along a strided axis of length L on z-spectral rows:

@@ -5,8 +5,8 @@
 namespace reg {
 template <>
 void adv_stage<float>(Spectral<float>& sp, const float* u, const fused::AdvEpi<float>& e, float2* U, float2* Zx,
-                      float2* Zy) {
-  fused::adv_stage_impl<float>(sp, u, e, U, Zx, Zy);
+                      float2* Zy, bool u_ready, bool emit) {
+  fused::adv_stage_impl<float>(sp, u, e, U, Zx, Zy, u_ready, emit);
 }
 template <>
 void adv2_stage<float>(Spectral<float>& sp, const float* uA, const fused::AdvEpi<float>& eA, const float* uB,

@@ -4,8 +4,8 @@
 namespace reg {
 template <>
 void adv_stage<double>(Spectral<double>& sp, const double* u, const fused::AdvEpi<double>& e, double2* U,
-                       double2* Zx, double2* Zy) {
-  fused::adv_stage_impl<double>(sp, u, e, U, Zx, Zy);
+                       double2* Zx, double2* Zy, bool u_ready, bool emit) {
+  fused::adv_stage_impl<double>(sp, u, e, U, Zx, Zy, u_ready, emit);
 }
 template <>
 void adv2_stage<double>(Spectral<double>& sp, const double* uA, const fused::AdvEpi<double>& eA, const double* uB,

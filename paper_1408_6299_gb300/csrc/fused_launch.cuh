@@ -50,9 +50,10 @@ void r2c(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, c
   throw StatusError{1, "unsupported last-axis length"};
 }
 
-template <typename T, int L, int NF, int EPI>
+template <typename T, int L, int NF, int EPI, int NE>
 void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
-           const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc, const AdvEpi<T>& advB) {
+           const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc, const AdvEpi<T>& advB,
+           const Emit<T>& em) {
   constexpr int M = L / 2;
   // single precision: 512 complex values per field and block for one field,
   // 1024 for more (4 and 8 rows at L = 256), so that the epilogue operand
@@ -62,24 +63,24 @@ void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, 
   constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NX == 1 || NX > 4 ? 8 : 4) * M)
                                      : row_elems<T>() / ((NX > 4 ? 8 : pow2_ceil(NX)) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
-  ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * NX * (fft_flops<M>() + 8.0 * M));
+  ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * (NX + NE) * (fft_flops<M>() + 8.0 * M));
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
-  k_rows_c2r_n<T, L, RB, NF, EPI><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc, advB);
+  k_rows_c2r_n<T, L, RB, NF, EPI, NE><<<grid, kThreads, 0, s>>>(in, zmask, adv, dv, g.rows, tw, twrc, advB, em);
   REG_LAUNCH();
 }
 
-template <typename T, int NF, int EPI>
+template <typename T, int NF, int EPI, int NE = 0>
 void c2r(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, const AdvEpi<T>& adv,
          const DivEpi<T>& dv, double bytes, const cx<T>* tw, const cx<T>* twrc,
-         const AdvEpi<T>& advB = AdvEpi<T>{}) {
+         const AdvEpi<T>& advB = AdvEpi<T>{}, const Emit<T>& em = Emit<T>{}) {
   switch (g.L) {
-    case 8: return c2r_L<T, 8, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 16: return c2r_L<T, 16, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 32: return c2r_L<T, 32, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 64: return c2r_L<T, 64, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 128: return c2r_L<T, 128, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 256: return c2r_L<T, 256, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
-    case 512: return c2r_L<T, 512, NF, EPI>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB);
+    case 8: return c2r_L<T, 8, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 16: return c2r_L<T, 16, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 32: return c2r_L<T, 32, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 64: return c2r_L<T, 64, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 128: return c2r_L<T, 128, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 256: return c2r_L<T, 256, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
+    case 512: return c2r_L<T, 512, NF, EPI, NE>(g, s, in, zmask, adv, dv, bytes, tw, twrc, advB, em);
   }
   throw StatusError{1, "unsupported last-axis length"};
 }
@@ -411,20 +412,32 @@ bool cols_pairs(const Spectral<T>& sp, const ColJob<T>* jobs, int nj, cudaStream
   }
 }
 
+// One advection stage on u. u_ready: U already holds the packed spectrum of u
+// (emitted by the previous stage's row pass), so no real-to-complex pass
+// runs. emit: the row pass leaves the spectrum of its out1 values in U for
+// the next stage.
 template <typename T>
-void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy) {
+void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy, bool u_ready,
+                    bool emit) {
   const Grid& g = sp.grid();
   cudaStream_t s = sp.stream();
   const cx<T>* tw = sp.twiddles(g.M);
   const cx<T>* twrc = sp.rc_twiddles();
-  RowsIn<T, 1> in1{{u}};
-  RowsOut<T, 1> out1{{U}};
-  r2c<T, 1, false>(g, s, in1, nullptr, out1, 0, tw, twrc);
+  if (!u_ready) {
+    RowsIn<T, 1> in1{{u}};
+    RowsOut<T, 1> out1{{U}};
+    r2c<T, 1, false>(g, s, in1, nullptr, out1, 0, tw, twrc);
+  }
   const int d = g.d;
   double bytes = (double)g.N * sizeof(T) *
                  (d + (e.G[0] ? d : 0) + (e.Sout ? d + 1 : 0) +
-                  (e.out1 ? d + (e.src ? 1 : (e.gm[0] ? 2 * d : 0)) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1) : 0));
+                  (e.out1 ? d + (e.src ? 1 : (e.gm[0] ? 2 * d : 0)) + (e.y ? 1 : 0) + (e.stage == 1 ? 2 : 1) -
+                                (e.out1_spectral_only ? 1 : 0)
+                          : 0) +
+                  (emit ? 1 : 0));
   DivEpi<T> none{};
+  Emit<T> em{};
+  em.out[0] = U;
   if (d == 3) {
     const ColJob<T> jobs[2] = {{0, U, Zx, nullptr}, {1, U, Zy, nullptr}};
     if (!cols_pairs<T>(sp, jobs, 2, s)) {
@@ -439,17 +452,19 @@ void adv_stage_impl(Spectral<T>& sp, const T* u, const AdvEpi<T>& e, cx<T>* U, c
       REG_CUDA(cudaStreamWaitEvent(s, sp.join_event(), 0));
     }
     RowsSpec<T, 3> in{{Zx, Zy, U}};
-    c2r<T, 3, EPI_ADV>(g, s, in, 1 << 2, e, none, bytes, tw, twrc);
+    if (emit) c2r<T, 3, EPI_ADV, 1>(g, s, in, 1 << 2, e, none, bytes, tw, twrc, AdvEpi<T>{}, em);
+    else c2r<T, 3, EPI_ADV>(g, s, in, 1 << 2, e, none, bytes, tw, twrc);
   } else {
     deriv<T>(g, sp, 0, U, Zy, nullptr, s);
     RowsSpec<T, 2> in{{Zy, U}};
-    c2r<T, 2, EPI_ADV>(g, s, in, 1 << 1, e, none, bytes, tw, twrc);
+    if (emit) c2r<T, 2, EPI_ADV, 1>(g, s, in, 1 << 1, e, none, bytes, tw, twrc, AdvEpi<T>{}, em);
+    else c2r<T, 2, EPI_ADV>(g, s, in, 1 << 1, e, none, bytes, tw, twrc);
   }
 }
 
 // Two advection stages of 3D fields uA and uB in one pass sequence: one
-// real-to-complex pass over both, the four strided passes (x on the second
-// stream), one complex-to-real pass of six spectra with both epilogues.
+// real-to-complex pass over both, the four strided passes, one
+// complex-to-real pass of six spectra with both epilogues.
 template <typename T>
 void adv2_stage_impl(Spectral<T>& sp, const T* uA, const AdvEpi<T>& eA, const T* uB, const AdvEpi<T>& eB,
                      cx<T>* const* Z) {

@@ -180,9 +180,12 @@ struct AdvEpi;
 template <typename T>
 struct DivEpi;
 }  // namespace fused
-// three packed-spectrum scratch buffers per call (Zx unused in 2D)
+// three packed-spectrum scratch buffers per call (Zx unused in 2D). u_ready:
+// U already holds the packed spectrum of u (no real-to-complex pass); emit:
+// the last pass leaves the packed spectrum of the stage's out1 in U.
 template <typename T>
-void adv_stage(Spectral<T>& sp, const T* u, const fused::AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy);
+void adv_stage(Spectral<T>& sp, const T* u, const fused::AdvEpi<T>& e, cx<T>* U, cx<T>* Zx, cx<T>* Zy,
+               bool u_ready = false, bool emit = false);
 // two 3D advection stages (fields uA, uB) sharing their passes; Z: six
 // spectral work arrays of Nc values
 template <typename T>

@@ -258,10 +258,14 @@ const T* vel_node(reg_ctx* c, const T* coef, int j, T* buf) {
   return buf;
 }
 
-// fused advection stage on u: k = -a.grad u [- gm.w], Heun stage update
+// fused advection stage on u: k = -a.grad u [- gm.w], Heun stage update.
+// u_ready: w.U already holds the spectrum of u (left there by the previous
+// stage); emit: leave the spectrum of out1 in w.U for the next stage;
+// spec_only: out1 is needed only as that spectrum (no real store).
 template <typename T>
 void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* y, T* out1, T* out2, T* Gkeep,
-         int stage, const T* src = nullptr, const T* sw = nullptr, T* Sout = nullptr) {
+         int stage, const T* src = nullptr, const T* sw = nullptr, T* Sout = nullptr, bool u_ready = false,
+         bool emit = false, bool spec_only = false) {
   Work<T>& w = work<T>(c);
   const long N = c->N(), Nc = c->g.Nc;
   fused::AdvEpi<T> e{};
@@ -279,7 +283,8 @@ void adv(reg_ctx* c, const T* u, const T* a, const T* gm, const T* wv, const T* 
   e.out2 = out2;
   e.h = (T)c->h();
   e.stage = stage;
-  adv_stage<T>(spectral<T>(c), u, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc));
+  e.out1_spectral_only = spec_only ? 1 : 0;
+  adv_stage<T>(spectral<T>(c), u, e, w.U.get(Nc), w.W.get(Nc), w.X.get(Nc), u_ready, emit);
 }
 
 // epilogue of an advection stage without stored-gradient source terms
@@ -313,8 +318,8 @@ void adv2(reg_ctx* c, const T* uA, const fused::AdvEpi<T>& eA, const T* uB, cons
 
 // grad u into G (d fields) through the fused stage passes
 template <typename T>
-void grad_fused(reg_ctx* c, const T* u, T* G) {
-  adv<T>(c, u, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, G, 1);
+void grad_fused(reg_ctx* c, const T* u, T* G, bool u_ready = false) {
+  adv<T>(c, u, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, G, 1, nullptr, nullptr, nullptr, u_ready);
 }
 
 // fused divergence stage on lam: k = div(a lam), Heun stage update; e carries
@@ -350,17 +355,22 @@ void state_steps(reg_ctx* c, const T* vcoef, int j0, int j1, T* gm, T* gmh, int 
   T* G = w.G.get(dN);
   T* va = w.va.get(dN);
   T* vb = w.vb.get(dN);
+  // each stage leaves the spectrum of its out1 in w.U for the next one; the
+  // predictor yh is needed only as that spectrum
+  bool ready = false;
   for (int j = j0; j < j1; ++j) {
     if (ck && c->ckpt > 0 && j % c->ckpt == 0)
       REG_CUDA(cudaMemcpyAsync(ck + (long)(j / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
     adv<T>(c, m, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, yh, acc, gm ? gm + (long)(j - base) * dN : nullptr,
-           1);
+           1, nullptr, nullptr, nullptr, ready, true, true);
+    const bool more = j + 1 < j1 || gm;  // the spectrum of m is read next
     adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, m, nullptr,
-           gmh ? gmh + (long)(j + 1 - base) * dN : nullptr, 2);
+           gmh ? gmh + (long)(j + 1 - base) * dN : nullptr, 2, nullptr, nullptr, nullptr, true, more);
+    ready = more;
   }
   if (ck && c->ckpt > 0 && j1 % c->ckpt == 0)
     REG_CUDA(cudaMemcpyAsync(ck + (long)(j1 / c->ckpt) * N, m, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
-  if (gm) grad_fused<T>(c, m, gm + (long)(j1 - base) * dN);
+  if (gm) grad_fused<T>(c, m, gm + (long)(j1 - base) * dN, ready);
 }
 
 // Recompute state gradients of segment [j0, j1] from the checkpoint at j0.
@@ -389,13 +399,16 @@ void recompute_segment_src(reg_ctx* c, const T* vcoef, const T* wcoef, int j0, i
   T* wa = w.wa.get(dN);
   T* src = w.src.get((size_t)(c->ckpt + 1) * N);
   REG_CUDA(cudaMemcpyAsync(m, w.ck.p + (long)(j0 / c->ckpt) * N, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
+  bool ready = false;  // w.U holds the spectrum of m
   for (int j = j0; j < j1; ++j) {
     adv<T>(c, m, vel_node<T>(c, vcoef, j, va), nullptr, nullptr, m, yh, acc, nullptr, 1, nullptr,
-           vel_node<T>(c, wcoef, j, wa), src + (long)(j - j0) * N);
-    adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, m, nullptr, nullptr, 2);
+           vel_node<T>(c, wcoef, j, wa), src + (long)(j - j0) * N, ready, true, true);
+    adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, m, nullptr, nullptr, 2, nullptr, nullptr,
+           nullptr, true, true);
+    ready = true;
   }
   adv<T>(c, m, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, nullptr,
-         vel_node<T>(c, wcoef, j1, wa), src + (long)(j1 - j0) * N);
+         vel_node<T>(c, wcoef, j1, wa), src + (long)(j1 - j0) * N, ready);
 }
 
 // Gradient slots available for node j (after ensure_segment)
@@ -613,7 +626,8 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
         const T* wA = vel_node<T>(c, wcoef, j, wa);
         fused::AdvEpi<T> sA = adv_epi<T>(c, vA, m, yhS, accS, 1, nullptr, wA, sj);
         if (j == 0) {
-          adv<T>(c, m, vA, nullptr, nullptr, m, yhS, accS, nullptr, 1, nullptr, wA, sj);
+          // the state's stage 1 leaves the spectrum of yhS for its stage 2
+          adv<T>(c, m, vA, nullptr, nullptr, m, yhS, accS, nullptr, 1, nullptr, wA, sj, false, true, true);
         } else {
           fused::AdvEpi<T> iB = adv_epi<T>(c, vA, acc, y, nullptr, 2);
           iB.src_from_a = 1;
@@ -623,7 +637,7 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
         }
         const T* vB = vel_node<T>(c, vcoef, j + 1, vb);
         if (j == 0) {
-          adv<T>(c, yhS, vB, nullptr, nullptr, accS, m, nullptr, nullptr, 2);
+          adv<T>(c, yhS, vB, nullptr, nullptr, accS, m, nullptr, nullptr, 2, nullptr, nullptr, nullptr, true);
           lincomb_t<T>(-h, sj, (T)0, nullptr, yh, N, c->s);
           lincomb_t<T>((T)(-0.5) * h, sj, (T)0, nullptr, acc, N, c->s);
         } else {
@@ -643,6 +657,10 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
     if (mtil)
       REG_CUDA(cudaMemcpyAsync(mtil + (long)c->n_t * N, y, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
   }
+  // each stage leaves the spectrum of its out1 in w.U for the next one (the
+  // state re-advance of a segment overwrites it); the predictor yh is needed
+  // only as that spectrum
+  bool ready = false;
   for (int seg = 0; seg * K < c->n_t && !(use_src && c->ckpt > 0 && c->d == 3); ++seg) {
     int j0 = seg * K, j1 = j0 + K;
     int base = 0;
@@ -650,9 +668,12 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
       if (use_src) recompute_segment_src<T>(c, vcoef, wcoef, j0, j1);
       else recompute_segment<T>(c, vcoef, j0, j1);
       base = j0;
+      ready = false;
     }
     for (int j = j0; j < j1; ++j) {
       const T* vA = vel_node<T>(c, vcoef, j, va);
+      const bool more = j + 1 < j1;  // the next stage of this segment reads the spectrum of y
+      const bool yh_ready = j > 0;
       if (use_src) {
         const T* s1 = w.src.p + (long)(j - base) * N;
         const T* s2 = w.src.p + (long)(j + 1 - base) * N;
@@ -660,9 +681,10 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
           lincomb_t<T>(-h, s1, (T)0, nullptr, yh, N, c->s);
           lincomb_t<T>((T)(-0.5) * h, s1, (T)0, nullptr, acc, N, c->s);
         } else {
-          adv<T>(c, y, vA, nullptr, nullptr, y, yh, acc, nullptr, 1, s1);
+          adv<T>(c, y, vA, nullptr, nullptr, y, yh, acc, nullptr, 1, s1, nullptr, nullptr, ready, true, true);
         }
-        adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, y, nullptr, nullptr, 2, s2);
+        adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), nullptr, nullptr, acc, y, nullptr, nullptr, 2, s2, nullptr,
+               nullptr, yh_ready, more);
         if (mtil)
           REG_CUDA(cudaMemcpyAsync(mtil + (long)(j + 1) * N, y, N * sizeof(T), cudaMemcpyDeviceToDevice, c->s));
       } else {
@@ -672,11 +694,12 @@ void gn_sweeps(reg_ctx* c, const T* vcoef, const T* wcoef, double* f) {
         if (j == 0) {
           transport_stage1<T>(nullptr, vA, g1, wA, nullptr, h, yh, acc, c->d, N, c->s);
         } else {
-          adv<T>(c, y, vA, g1, wA, y, yh, acc, nullptr, 1);
+          adv<T>(c, y, vA, g1, wA, y, yh, acc, nullptr, 1, nullptr, nullptr, nullptr, ready, true, true);
         }
         adv<T>(c, yh, vel_node<T>(c, vcoef, j + 1, vb), g2, vel_node<T>(c, wcoef, j + 1, wb), acc, y, nullptr,
-               nullptr, 2);
+               nullptr, 2, nullptr, nullptr, nullptr, yh_ready, more);
       }
+      ready = more;
     }
   }
   // lam~_1 = -m~_1
@@ -693,19 +716,23 @@ namespace {
 // Fourier-diagonal tail (FP64): out = beta (C (x) A) V + K^gamma F
 // (App. A Eq. control-equation-expansion; Eq. eliminated-control). F may be null.
 // ---------------------------------------------------------------------------
+// Without the Leray projection the body force passes the tail unchanged, so it
+// is added in physical space and only V is transformed.
 void tail(reg_ctx* c, const double* V, const double* F, double* out) {
   const long Nc = c->g.Nc, N = c->N();
   const int ncd = c->n_c * c->d;
   double2* SV = c->SV.get((size_t)ncd * Nc);
   double2* SF = c->SF.get((size_t)ncd * Nc);
   Spectral<double>& sp = *c->sp64;
+  const bool fspec = F && c->stokes;
   for (int q = 0; q < ncd; ++q) {
     sp.fwd(V + q * N, SV + q * Nc);
-    if (F) sp.fwd(F + q * N, SF + q * Nc);
+    if (fspec) sp.fwd(F + q * N, SF + q * Nc);
   }
-  spec_tail(c->g, c->s, SV, F ? SF : nullptr, SF, c->n_c, c->beta, c->Cg_dev.p, c->rtype, c->stokes,
+  spec_tail(c->g, c->s, SV, fspec ? SF : nullptr, SF, c->n_c, c->beta, c->Cg_dev.p, c->rtype, c->stokes,
             c->g.B > 1 ? c->betas_dev.p : nullptr);
   for (int q = 0; q < ncd; ++q) sp.inv(SF + q * Nc, out + q * N);
+  if (F && !fspec) lincomb_t<double>(1.0, out, 1.0, F, out, (long)ncd * N, c->s);
 }
 
 void precond(reg_ctx* c, const double* r, double* z) {
