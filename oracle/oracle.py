@@ -291,6 +291,20 @@ class Problem:
         self._call("orc_detF", _ptr(v), _ptr(out))
         return out
 
+    def detF_refined(self, v, refine, substeps=1):
+        """det F_1 of App. D Eq. def-grad on the grid refined `refine` times per
+        axis with substeps * n_t Heun steps: the velocity coefficients are
+        carried to the fine grid by trigonometric interpolation without their
+        Nyquist modes (trig_interp, nyquist="drop": the coarse first
+        derivatives, reading R1, do not see those) and the oracle's own
+        F-equation solve runs there."""
+        v = _f64(v).reshape(self.coef_shape())
+        nf = tuple(refine * k for k in self.n)
+        vf = np.stack([np.stack([trig_interp(v[l, i], nf, "drop") for i in range(self.d)])
+                       for l in range(self.n_c)])
+        Pf = Problem(nf, self.n_t * substeps, self.n_c, self.beta, self.reg, self.stokes)
+        return Pf.detF(vf)
+
     def defgrad(self, v):
         """F_1 of App. D Eq. def-grad, shape (d, d, *n)."""
         v = _f64(v).reshape(self.coef_shape())
@@ -400,6 +414,32 @@ def cheb_gram(n_c):
     C = np.empty((n_c, n_c))
     lib().orc_cheb_gram(int(n_c), _ptr(C))
     return C
+
+
+def trig_interp(u, nf, nyquist="split"):
+    """The trigonometric interpolant of the periodic grid values u (shape n) at
+    the nodes of the grid nf (nf_a a multiple of n_a): per axis, the DFT
+    coefficients of |k| < n_a/2 are kept and every finer mode is zero. The
+    Nyquist coefficient k = n_a/2 is split in halves between +n_a/2 and -n_a/2
+    (nyquist="split": the real interpolant of the samples) or dropped
+    (nyquist="drop": the part of u that the masked first derivatives of the
+    Nyquist reading R1 differentiate). numpy's FFT is the transform; the result
+    is scaled by nf_a / n_a so that it holds point values."""
+    out = np.asarray(u, dtype=np.float64)
+    for a, m in enumerate(nf):
+        n = out.shape[a]
+        if m == n:
+            continue
+        U = np.moveaxis(np.fft.fft(out, axis=a), a, 0)
+        W = np.zeros((m,) + U.shape[1:], dtype=np.complex128)
+        h = n // 2
+        W[:h] = U[:h]
+        W[m - h + 1:] = U[h + 1:]
+        if nyquist == "split":
+            W[h] = 0.5 * U[h]
+            W[m - h] = 0.5 * U[h]
+        out = np.real(np.fft.ifft(np.moveaxis(W, 0, a), axis=a)) * (m / n)
+    return out
 
 
 def num_threads():

@@ -208,5 +208,8 @@ void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out,
                   const double* Ci_dev, int reg, const double* betas = nullptr);
 // Gaussian filter exp(-sigma^2 |k|^2 / 2) of one packed FP64 field (out may not alias U)
 void spec_gauss(const Grid& g, cudaStream_t s, double2* U, double2* out, double sigma);
+// trigonometric interpolation of nfields packed FP64 spectra of grid c onto the
+// finer grid f (every axis refined by a factor >= 2; one problem, no stacking)
+void spec_upsample(const Grid& c, const Grid& f, cudaStream_t s, const double2* P, double2* Q, int nfields);
 
 }  // namespace reg

@@ -979,6 +979,35 @@ void detF(reg_ctx* c, const double* v, int substeps, double st[4], double* det_o
   stats(det, N, red(c), c->s, st);
 }
 
+reg_ctx* create_ctx(int d, const int64_t* n, int n_t, int n_c, double beta, int reg_type, int stokes, int precision,
+                    int ckpt_every, void* cuda_stream, int batch);
+
+// det F_1 statistics on a grid refined `refine` times per axis: the velocity,
+// band-limited on the context's grid, is carried to the finer grid exactly by
+// trigonometric interpolation (its spectrum padded with zeros), and Eq.
+// def-grad is integrated there, where the products of the F-equation are
+// resolved. det_out (may be null): the N * refine^d values of the fine grid.
+void detF_refined(reg_ctx* c, const double* v, int substeps, int refine, double st[4], double* det_out) {
+  if (refine == 1) return detF(c, v, substeps, st, det_out);
+  if (c->g.B > 1) throw StatusError{REG_EINVAL, "refined det F needs a single problem"};
+  int64_t nf[3] = {1, 1, 1};
+  for (int a = 0; a < c->d; ++a) {
+    nf[a] = (int64_t)c->g.n[a] * refine;
+    if (nf[a] > 512) throw StatusError{REG_EINVAL, "refined grid exceeds 512 points per axis"};
+  }
+  std::unique_ptr<reg_ctx> f(create_ctx(c->d, nf, c->n_t, c->n_c, c->beta, c->rtype, c->stokes, REG_FP64, 0, c->s, 1));
+  const int ncd = c->n_c * c->d;
+  const long N = c->N(), Nc = c->g.Nc;
+  double2* P = c->SV.get((size_t)ncd * Nc);
+  for (int q = 0; q < ncd; ++q) c->sp64->fwd(v + q * N, P + q * Nc);
+  double2* Q = f->SV.get((size_t)ncd * f->g.Nc);
+  spec_upsample(c->g, f->g, c->s, P, Q, ncd);
+  double* vf = f->vlin.get(f->ncdN());
+  for (int q = 0; q < ncd; ++q) f->sp64->inv(Q + q * f->g.Nc, vf + q * f->N());
+  detF(f.get(), vf, substeps, st, det_out);
+  REG_CUDA(cudaStreamSynchronize(c->s));  // the fine context's buffers are freed on return
+}
+
 // det F_1 and grid-angle statistics from one F_1 (either field output may be null)
 void deform_measures(reg_ctx* c, const double* v, int substeps, double det_st[4], double ang_st[4], double* det_out,
                      double* ang_out) {
@@ -1276,7 +1305,7 @@ int solve(reg_ctx* c, double* v, const reg_solve_opts& o, reg_solve_report& R) {
   objective(c, v, pt);
   R.dist_rel = base > 0 ? (2.0 * pt[0] / c->hd) / base : 0.0;
   R.cfl = cfl(c, v);
-  if (o.detF_substeps > 0) detF(c, v, o.detF_substeps, R.detF, nullptr);
+  if (o.detF_substeps > 0) detF_refined(c, v, o.detF_substeps, o.detF_refine > 1 ? o.detF_refine : 1, R.detF, nullptr);
   REG_CUDA(cudaStreamSynchronize(c->s));
   R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   R.status = status;
@@ -2038,6 +2067,27 @@ reg_status reg_detF(reg_ctx* ctx, const double* v, int substeps, double* stats_o
   API_END
 }
 
+reg_status reg_detF_refined(reg_ctx* ctx, const double* v, int substeps, int refine, double* stats_out,
+                            double* detF_out) {
+  API_BEGIN(ctx)
+  if (substeps < 1) throw StatusError{REG_EINVAL, "substeps must be >= 1"};
+  if (refine != 1 && refine != 2 && refine != 4) throw StatusError{REG_EINVAL, "refine must be 1, 2 or 4"};
+  if (!stats_out) throw StatusError{REG_EINVAL, "stats is null"};
+  const double* vd = input_ptr(c_, v, c_->ncdN(), 0);
+  long nfine = c_->N();
+  for (int a = 0; a < c_->d; ++a) nfine *= refine;
+  double st[4];
+  if (detF_out) {
+    Output o(c_, detF_out, nfine, c_->stage_out);
+    detF_refined(c_, vd, substeps, refine, st, o.dev);
+    o.finish();
+  } else {
+    detF_refined(c_, vd, substeps, refine, st, nullptr);
+  }
+  for (int i = 0; i < 4; ++i) stats_out[i] = st[i];
+  API_END
+}
+
 reg_status reg_cfl(reg_ctx* ctx, const double* v, double* cfl_out) {
   API_BEGIN(ctx)
   if (!cfl_out) throw StatusError{REG_EINVAL, "cfl_out is null"};
@@ -2190,6 +2240,7 @@ void reg_solve_opts_default(reg_solve_opts* o) {
   o->step_memory = 1;
   o->stop_rule = REG_STOP_GRAD_REL;
   o->tau_J = 1e-3;
+  o->detF_refine = 1;
 }
 
 reg_status reg_solve_lockstep(const reg_problem* problems, int count, int precision, const reg_solve_opts* opts,

@@ -11,6 +11,7 @@
 // mode k' with -k' to act on the two halves separately.
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 #include <stdexcept>
 
@@ -671,6 +672,60 @@ void spec_precond(const Grid& g, cudaStream_t s, const double2* R, double2* out,
 
 void spec_gauss(const Grid& g, cudaStream_t s, double2* U, double2* out, double sigma) {
   k_spec_gauss<<<blocks_for(g.Nc), 256, 0, s>>>(U, out, args(g), sigma * sigma);
+  REG_LAUNCH();
+}
+
+// Trigonometric interpolation onto a grid refined per axis: the packed
+// spectrum Q of the fine grid f from the packed spectrum P of the coarse grid
+// c (nfields fields each; scale = N_f / N_c, so the fine inverse transform
+// returns point values). A mode with |k_a| < n_a/2 on every axis keeps its
+// coefficient; every other mode is zero, the coarse Nyquist modes included:
+// the coarse derivatives treat those as constants (first derivatives and the
+// Leray projection use the masked wavenumber), so the interpolated field is
+// the part of the velocity that the coarse operators differentiate, and a
+// velocity that is divergence-free on the coarse grid stays divergence-free.
+// On the last axis the coarse slot 0 (DC + i Nyquist, both Hermitian in the
+// other axes) is unpacked and its DC half goes to the fine slot 0.
+__global__ void k_spec_upsample(const double2* __restrict__ P, double2* __restrict__ Q, GridArgs c, GridArgs f,
+                                int nfields, double scale) {
+  const long total = (long)nfields * f.Nc;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const long fld = t / f.Nc, q = t % f.Nc;
+    const ModeIdx m = decode(q, f.d, f.n, f.M);
+    bool zero = m.j[f.d - 1] >= c.M;
+    long row = 0, nrow = 0;  // coarse row of k' and of -k'
+    for (int a = 0; a < f.d - 1 && !zero; ++a) {
+      const long i = m.j[a];
+      const long k = i < f.n[a] / 2 ? i : i - f.n[a];
+      const long h = c.n[a] / 2;
+      if (k >= h || k <= -h) {
+        zero = true;
+        break;
+      }
+      const long ci = (k + c.n[a]) % c.n[a];
+      row = row * c.n[a] + ci;
+      nrow = nrow * c.n[a] + (c.n[a] - ci) % c.n[a];
+    }
+    double2 out = make_double2(0.0, 0.0);
+    if (!zero) {
+      const double2* Pf = P + fld * c.Nc;
+      const long kz = m.j[f.d - 1];
+      if (kz > 0) {
+        const double2 z = Pf[row * c.M + kz];
+        out = make_double2(scale * z.x, scale * z.y);
+      } else {  // the DC half of the coarse slot 0: (z + conj(zn)) / 2
+        const double2 z = Pf[row * c.M], zn = Pf[nrow * c.M];
+        out = make_double2(0.5 * scale * (z.x + zn.x), 0.5 * scale * (z.y - zn.y));
+      }
+    }
+    Q[fld * f.Nc + q] = out;
+  }
+}
+
+void spec_upsample(const Grid& c, const Grid& f, cudaStream_t s, const double2* P, double2* Q, int nfields) {
+  const long total = (long)nfields * f.Nc;
+  const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+  k_spec_upsample<<<blocks, 256, 0, s>>>(P, Q, args(c), args(f), nfields, (double)f.N / (double)c.N);
   REG_LAUNCH();
 }
 

@@ -42,6 +42,7 @@ class SolveOpts(ctypes.Structure):
         ("step_memory", ctypes.c_int),
         ("stop_rule", ctypes.c_int),
         ("tau_J", ctypes.c_double),
+        ("detF_refine", ctypes.c_int),
     ]
 
     @classmethod
@@ -170,6 +171,7 @@ _SIGNATURES = {
     "reg_transport": [_vp, _vp, _vp, _vp],
     "reg_transport_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp],
     "reg_detF": [_vp, _vp, ctypes.c_int, _vp, _vp],
+    "reg_detF_refined": [_vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp],
     "reg_cfl": [_vp, _vp, _vp],
     "reg_grid_angle": [_vp, _vp, ctypes.c_int, _vp, _vp],
     "reg_displacement": [_vp, _vp, _vp],
@@ -453,6 +455,15 @@ class Registration:
         b, kb = _addr(out, self.N)
         st = (ctypes.c_double * 4)()
         self._check(self.L.reg_detF(self.ctx, a, int(substeps), st, b))
+        return tuple(st)
+
+    def detF_refined(self, v, substeps=1, refine=2, out=None):
+        """det F_1 statistics (min, max, mean, std) on a grid refined `refine`
+        times per axis; out (optional): the fine-grid field (N * refine^d values)."""
+        a, ka = _addr(v, self.ncdN)
+        b, kb = _addr(out, self.N * int(refine) ** self.d)
+        st = (ctypes.c_double * 4)()
+        self._check(self.L.reg_detF_refined(self.ctx, a, int(substeps), int(refine), st, b))
         return tuple(st)
 
     def cfl(self, v):

@@ -337,3 +337,26 @@ def test_mixed_matvec_with_paired_column_passes(n):
         assert err < MIXED_TOL, (ckpt, err)
         assert relmax(host(Hv), ref) < 10 * MIXED_TOL, ckpt
         R.close()
+
+
+# ---------------------------------------------------------------------------
+# det F_1 on a refined grid (reg_detF_refined): trigonometric interpolation of
+# the velocity, with Nyquist content (white noise) and n_c = 2, then Eq.
+# def-grad on the finer grid
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,refine,n_c", [((16, 16), 2, 1), ((16, 16), 4, 2), ((8, 16, 16), 2, 2)],
+                         ids=["16x16-r2", "16x16-r4-nc2", "8x16x16-r2-nc2"])
+def test_refined_detF_matches_oracle(n, refine, n_c):
+    r = np.random.default_rng(808)
+    v = synth.white_noise_velocity(n, r, n_c, 0.05)
+    c = dict(n=n, n_t=4, n_c=n_c, beta=1e-2, reg=1, stokes=False)
+    R, P = pair(c)
+    out = empty(tuple(refine * k for k in n))
+    st = R.detF_refined(cuda(v), 2, refine, out)
+    ref = P.detF_refined(v, refine, 2)
+    assert relmax(host(out), ref) < 1e-12
+    assert abs(st[0] - ref.min()) < 1e-12 and abs(st[1] - ref.max()) < 1e-12
+    assert abs(st[2] - ref.mean()) < 1e-12 and abs(st[3] - ref.std()) < 1e-10
+    # refine = 1 is the plain evaluation
+    assert R.detF_refined(cuda(v), 1, 1) == R.detF(cuda(v), 1)

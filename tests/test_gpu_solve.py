@@ -1,11 +1,12 @@
 """Inexact Gauss-Newton-Krylov solves (Alg. 1) on the GPU.
 
 The 3D Stokes scheme with n_c = 3 Chebyshev coefficients reaches the relative
-gradient reduction 1e-2 with a divergence-free iterate (to rounding); det F_1
-of App. D Eq. def-grad stays within 1e-4 of one there, the remaining deviation
-being the spatial aliasing of the pseudospectral F-equation (it does not
-shrink with the time step). A smaller Stokes problem matches the oracle's
-solve iterate by iterate."""
+gradient reduction 1e-2 with a divergence-free iterate (to rounding), and det
+F_1 of App. D Eq. def-grad is within 1e-6 of one. On the 64^3 grid itself the
+F-equation's products are not resolved and det F_1 - 1 stalls near 5e-5 for
+any time step; the check therefore integrates Eq. def-grad on the grid refined
+twice per axis (the velocity interpolated exactly), with 4 n_t steps. A
+smaller Stokes problem matches the oracle's solve iterate by iterate."""
 import numpy as np
 import pytest
 
@@ -24,12 +25,15 @@ def test_stokes_3d_solve_reaches_tolerance_with_unit_jacobian(precision):
     mR = P.state(c["v_true"], c["mT"])[-1]
     R.set_images(cuda(c["mT"]), cuda(mR))
     v = cuda(np.zeros(R.coef_shape()))
-    rep = R.solve(v, grad_rtol=1e-2, detF_substeps=16)
+    rep = R.solve(v, grad_rtol=1e-2, detF_substeps=4, detF_refine=2)
     assert rep["status"] == 0
     assert rep["g_inf"] <= 1e-2 * rep["g0_inf"]
     assert rep["J"] < rep["J0"]
     dmin, dmax = rep["detF"][0], rep["detF"][1]
-    assert abs(dmin - 1) < 1e-4 and abs(dmax - 1) < 1e-4, rep["detF"]
+    assert abs(dmin - 1) <= 1e-6 and abs(dmax - 1) <= 1e-6, rep["detF"]
+    # the unrefined evaluation stalls at the spatial error
+    coarse = R.detF(v, 4)
+    assert max(abs(coarse[0] - 1), abs(coarse[1] - 1)) > 1e-5
     # the iterate stays divergence-free (pressure elimination, Sec. 3.3.4)
     div = np.zeros(c["n"])
     Pg = O.Problem(c["n"], 2)

@@ -930,3 +930,67 @@ def test_cfl_of_a_chebyshev_velocity_by_hand():
     a = -0.35
     w = np.stack([a * np.sin(X[1]), np.zeros(n)])[None]
     assert abs(O.Problem(n, n_t).cfl(w) - abs(a) * n[0] / (2 * np.pi) / n_t) <= 1e-15
+
+
+# ---------------------------------------------------------------------------
+# det F_1 on a refined grid (App. D Eq. def-grad): trigonometric interpolation
+# of the velocity onto the finer grid, then the same F-equation solve there
+# ---------------------------------------------------------------------------
+
+def test_trig_interp_reproduces_trigonometric_polynomials():
+    # modes below Nyquist are kept exactly; the Nyquist mode cos(n x / 2),
+    # sampled as (-1)^j, is continued as the cosine itself
+    n, nf = (8, 16), (32, 64)
+    X = synth.coords(n)
+    Xf = synth.coords(nf)
+    u = 0.3 + np.sin(X[0]) * np.cos(3 * X[1]) + 0.5 * np.cos(2 * X[0] - 5 * X[1]) + 0.25 * np.cos(4 * X[0])
+    uf = 0.3 + np.sin(Xf[0]) * np.cos(3 * Xf[1]) + 0.5 * np.cos(2 * Xf[0] - 5 * Xf[1]) + 0.25 * np.cos(4 * Xf[0])
+    assert np.abs(O.trig_interp(u, nf) - uf).max() < 1e-14
+    # a field with Nyquist content on both axes, in 3D
+    n3, nf3 = (4, 8, 8), (8, 16, 32)
+    Y = synth.coords(n3)
+    Yf = synth.coords(nf3)
+    w = np.cos(2 * Y[0]) * np.cos(4 * Y[2]) + np.sin(Y[1] + Y[2])
+    wf = np.cos(2 * Yf[0]) * np.cos(4 * Yf[2]) + np.sin(Yf[1] + Yf[2])
+    assert np.abs(O.trig_interp(w, nf3) - wf).max() < 1e-14
+    # dropping the Nyquist modes keeps only what the masked derivatives see
+    assert np.abs(O.trig_interp(w, nf3, "drop") - np.sin(Yf[1] + Yf[2])).max() < 1e-14
+    assert np.abs(O.trig_interp(u, nf, "drop") - (uf - 0.25 * np.cos(4 * Xf[0]))).max() < 1e-14
+
+
+def test_refined_detF_of_a_divergence_free_nyquist_field():
+    # v = (cos(n x2 / 2), 0) is a Nyquist mode: divergence-free, with zero masked
+    # derivatives, so F_1 = I on the coarse grid; the refined evaluation drops
+    # the mode and must give det F_1 = 1 as well
+    n = (16, 16)
+    X = synth.coords(n)
+    v = np.zeros((1, 2) + n)
+    v[0, 0] = 0.3 * np.cos(8 * X[1])
+    assert np.abs(O.Problem(n, 4).detF(v) - 1).max() < 1e-14
+    assert np.abs(O.Problem(n, 4).detF_refined(v, 2) - 1).max() < 1e-14
+
+
+def test_refined_detF_of_a_shear_is_exact():
+    n = (16, 16)
+    X = synth.coords(n)
+    v = np.zeros((1, 2) + n)
+    v[0, 0] = 0.8 * np.sin(X[1])
+    for r in (2, 4):
+        assert np.abs(O.Problem(n, 5).detF_refined(v, r) - 1).max() < 1e-13
+
+
+def test_refined_detF_converges_at_second_order():
+    # a divergence-free velocity with modes up to |k| = 6 on 16^2: on the coarse
+    # grid det F_1 - 1 stalls at a spatial error; four times finer it falls by
+    # about 4 per doubling of n_t (Heun is second order) and ends far below
+    n = (16, 16)
+    v = synth.velocity_field(n, rng(3), 6, 0.4, divergence_free=True)[None]
+    coarse, fine = [], []
+    for n_t in (16, 32, 64):
+        P = O.Problem(n, n_t)
+        coarse.append(np.abs(P.detF(v) - 1).max())
+        fine.append(np.abs(P.detF_refined(v, 4) - 1).max())
+    assert abs(coarse[2] / coarse[0] - 1) < 0.05
+    for a, b in zip(fine, fine[1:]):
+        assert 3.3 < a / b < 4.7, fine
+    assert fine[2] < coarse[2] / 100
