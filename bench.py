@@ -320,10 +320,15 @@ def batch_sample(count, workers):
     solve_pairs(pairs[:min(4, count)], workers, "executor")  # warm-up: tuning, tables
     solve_pairs(pairs[:min(4, count)], workers, "lockstep")
     tl, reps = solve_pairs(pairs, workers, "lockstep")
+    os.environ["REG_LOCKSTEP_GRAPHS"] = "0"  # the same lockstep solve with host-driven loops
+    th, _ = solve_pairs(pairs, workers, "lockstep")
+    del os.environ["REG_LOCKSTEP_GRAPHS"]
     tb, repb = solve_pairs(pairs, workers, "executor")
     ts, _ = solve_pairs(pairs, 1, "executor")
     ok = sum(1 for r in reps if r["status"] == 0 and r["g_inf"] <= 1e-2 * r["g0_inf"])
-    return {"pairs": count, "lockstep_solves_per_s": count / tl, "executor_solves_per_s": count / tb,
+    return {"pairs": count, "lockstep_solves_per_s": count / tl,
+            "lockstep_device_loops": sum(r["device_loops"] for r in reps),
+            "lockstep_host_loops_solves_per_s": count / th, "executor_solves_per_s": count / tb,
             "executor_workers": workers, "sequential_solves_per_s": count / ts, "speedup_vs_sequential": ts / tl,
             "converged": ok, "mean_outer": sum(r["outer"] for r in reps) / count,
             "mean_matvecs": sum(r["matvecs"] for r in reps) / count,

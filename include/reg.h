@@ -299,6 +299,8 @@ typedef struct {
   double J_prev;        /* objective of the previous iterate (C1) */
   double dv_inf;        /* ||v_{k-1} - v_k||_inf of the last step (C2) */
   double v_inf;         /* ||v_k||_inf of the final iterate (C2) */
+  int device_loops;     /* reg_solve_lockstep: 1 when the problem's PCG and line-search loops ran
+                           on the device (conditional CUDA graphs), 0 when the host drove them */
 } reg_solve_report;
 
 /* Fill opts with the defaults above (grad_rtol 1e-2, max_outer 50, Krylov
@@ -358,7 +360,13 @@ REG_API reg_status reg_solve_batched(const reg_problem* problems, int count, int
  * or device memory; reports (may be NULL): one per problem, in the order of
  * `problems`. Returns the status of the first failing stack; a problem that
  * ends with REG_EMAXIT does not fail its stack. det F statistics are not
- * computed (detF_substeps is ignored). */
+ * computed (detF_substeps is ignored). With the Krylov method and no CFL bound
+ * the PCG and line-search loops of a stack run on the device: each is one
+ * CUDA graph whose conditional WHILE node iterates a check kernel (per-problem
+ * forcing-term, curvature and Armijo decisions, the same operations as the
+ * host loop) and an IF node with one iteration, so the host waits once per
+ * loop instead of once per reduction (report device_loops = 1; the
+ * environment variable REG_LOCKSTEP_GRAPHS=0 keeps the host-driven loops). */
 REG_API reg_status reg_solve_lockstep(const reg_problem* problems, int count, int precision,
                                       const reg_solve_opts* opts, reg_solve_report* reports, int max_stack);
 

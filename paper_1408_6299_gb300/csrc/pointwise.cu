@@ -404,6 +404,207 @@ void seg_reduce(int op, const double* a, const double* b, int K, int B, long N1,
   REG_CUDA(cudaStreamSynchronize(s));
 }
 
+void seg_reduce_dev(int op, const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                    double* out_dev) {
+  if (B > 65535) throw StatusError{1, "more than 65535 stacked problems"};
+  int nb = (int)(((long)K * N1 + 8L * kRedThreads - 1) / (8L * kRedThreads));  // as seg_reduce: the same sums
+  nb = nb < 1 ? 1 : (nb > 32 ? 32 : nb);
+  dim3 grid((unsigned)nb, (unsigned)B);
+  switch (op) {
+    case RED_DOT: k_seg_reduce<RED_DOT><<<grid, kRedThreads, 0, s>>>(a, b, K, B, N1, nb, scratch); break;
+    default: k_seg_reduce<RED_SQDIFF><<<grid, kRedThreads, 0, s>>>(a, b, K, B, N1, nb, scratch); break;
+  }
+  REG_LAUNCH();
+  k_seg_final<<<(B + 127) / 128, 128, 0, s>>>(scratch, nb, B, 0, out_dev);
+  REG_LAUNCH();
+}
+void seg_dot_dev(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                 double* out_dev) {
+  seg_reduce_dev(RED_DOT, a, b, K, B, N1, scratch, s, out_dev);
+}
+void seg_sqdiff_dev(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                    double* out_dev) {
+  seg_reduce_dev(RED_SQDIFF, a, b, K, B, N1, scratch, s, out_dev);
+}
+
+// ---------------------------------------------------------------------------
+// device-driven lockstep loops: one block of kLkThreads threads walks the B
+// problems; the handles are set by thread 0 after a block-wide OR
+// ---------------------------------------------------------------------------
+constexpr int kLkThreads = 256;
+#define LK(slot, q) lk[(long)(slot) * B + (q)]
+
+__global__ void k_lk_pcg_init(double* lk, int* ctl, int B) {
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    LK(LK_ONE, q) = 1.0;
+    LK(LK_ZERO, q) = 0.0;
+    LK(LK_MONE, q) = -1.0;
+    LK(LK_ON, q) = LK(LK_ACT, q);
+    LK(LK_ETA, q) = fmin(0.5, sqrt(LK(LK_G2, q) / LK(LK_G02, q)));
+    LK(LK_NEGC, q) = 0.0;
+    LK(LK_KEEP, q) = 1.0;
+    LK(LK_PCG, q) = LK(LK_MV, q) = LK(LK_NPDE, q) = LK(LK_LS, q) = 0.0;
+    LK(LK_STATUS, q) = 0.0;
+  }
+  if (threadIdx.x < LC_COUNT) ctl[threadIdx.x] = 0;
+}
+
+__global__ void k_lk_pcg_check(double* lk, int* ctl, int B, int cap, int maxit, cudaGraphConditionalHandle h_if,
+                               cudaGraphConditionalHandle h_while) {
+  int any = 0;
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    if (LK(LK_ON, q) == 0.0) continue;
+    const double rn2 = LK(LK_RN2, q);
+    if (LK(LK_ACT, q) != 0.0 && !isfinite(rn2)) {
+      LK(LK_ACT, q) = 0.0;
+      LK(LK_STATUS, q) = 5.0;  // REG_ENONFINITE
+    }
+    if (LK(LK_ACT, q) == 0.0 || sqrt(rn2) <= __dmul_rn(LK(LK_ETA, q), LK(LK_G2, q))) LK(LK_ON, q) = 0.0;
+    else any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int it = ctl[LC_IT];
+    const int run = any && ctl[LC_PIT] < maxit;
+    ctl[LC_ON] = any;
+    if (run) ctl[LC_IT] = it + 1;
+    cudaGraphSetConditional(h_if, run ? 1u : 0u);
+    cudaGraphSetConditional(h_while, (run && it + 1 < cap) ? 1u : 0u);
+  }
+}
+
+__global__ void k_lk_pcg_alpha(double* lk, int* ctl, int B) {
+  const int pit = ctl[LC_PIT];
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    double a = 0.0, negc = 0.0;
+    if (LK(LK_ON, q) != 0.0) {
+      LK(LK_MV, q) += 1.0;
+      LK(LK_NPDE, q) += 2.0;
+      LK(LK_PCG, q) += 1.0;
+      const double php = LK(LK_PHP, q);
+      if (LK(LK_ACT, q) != 0.0 && !isfinite(php)) {
+        LK(LK_ACT, q) = 0.0;
+        LK(LK_STATUS, q) = 5.0;
+      }
+      if (LK(LK_ACT, q) == 0.0) {
+        LK(LK_ON, q) = 0.0;
+      } else if (php <= 0.0) {
+        if (pit == 0) negc = 1.0;  // the steepest-descent direction
+        LK(LK_ON, q) = 0.0;
+      } else {
+        a = LK(LK_RZ, q) / php;
+      }
+    }
+    LK(LK_A, q) = a;
+    LK(LK_NEGC, q) = negc;
+    LK(LK_KEEP, q) = 1.0 - negc;
+  }
+}
+
+__global__ void k_lk_pcg_beta(double* lk, int* ctl, int B) {
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    double mz = 0.0, bt = 1.0;
+    if (LK(LK_ON, q) != 0.0) {
+      mz = -1.0;
+      bt = LK(LK_RZN, q) / LK(LK_RZ, q);
+      LK(LK_RZ, q) = LK(LK_RZN, q);
+    }
+    LK(LK_MZ, q) = mz;
+    LK(LK_BT, q) = bt;
+  }
+  if (threadIdx.x == 0) ctl[LC_PIT] += 1;
+}
+
+__global__ void k_lk_ls_init(double* lk, int* ctl, int B, double hd) {
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    LK(LK_SLOPE, q) = __dmul_rn(LK(LK_SLOPE, q), hd);
+    const bool act = LK(LK_ACT, q) != 0.0;
+    LK(LK_ALPHA, q) = act ? 1.0 : 0.0;
+    LK(LK_SRCH, q) = act ? 1.0 : 0.0;
+  }
+  if (threadIdx.x == 0) ctl[LC_LST] = 0;
+}
+
+__global__ void k_lk_ls_check(double* lk, int* ctl, int B, int max_bt, cudaGraphConditionalHandle h_if,
+                              cudaGraphConditionalHandle h_while) {
+  int any = 0;
+  for (int q = threadIdx.x; q < B; q += blockDim.x)
+    if (LK(LK_SRCH, q) != 0.0) any = 1;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int t = ctl[LC_LST];
+    const int run = any && t < max_bt;
+    if (run) ctl[LC_LST] = t + 1;
+    cudaGraphSetConditional(h_if, run ? 1u : 0u);
+    cudaGraphSetConditional(h_while, run ? 1u : 0u);
+  }
+}
+
+__global__ void k_lk_ls_armijo(double* lk, int B, double hd, double c1, double rho) {
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    if (LK(LK_SRCH, q) == 0.0) continue;
+    LK(LK_LS, q) += 1.0;
+    LK(LK_NPDE, q) += 1.0;
+    // J_t = 1/2 h_d d2 + 1/2 h_d r2, each part scaled as the host scales it
+    const double half_hd = __dmul_rn(0.5, hd);
+    const double jt = __dadd_rn(__dmul_rn(LK(LK_D2, q), half_hd), __dmul_rn(LK(LK_R2, q), half_hd));
+    LK(LK_JT, q) = jt;
+    const double a = LK(LK_ALPHA, q);
+    const double bound = __dadd_rn(LK(LK_J, q), __dmul_rn(__dmul_rn(c1, a), LK(LK_SLOPE, q)));
+    if (isfinite(jt) && jt <= bound) LK(LK_SRCH, q) = 0.0;
+    else LK(LK_ALPHA, q) = __dmul_rn(a, rho);
+  }
+}
+
+__global__ void k_lk_ls_final(double* lk, int B, int status_ls) {
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    if (LK(LK_SRCH, q) != 0.0) {
+      LK(LK_ACT, q) = 0.0;
+      LK(LK_STATUS, q) = (double)status_ls;
+      LK(LK_ALPHA, q) = 0.0;
+    }
+    if (LK(LK_ACT, q) == 0.0) LK(LK_ALPHA, q) = 0.0;
+  }
+}
+#undef LK
+
+void lk_pcg_init(double* lk, int* ctl, int B, cudaStream_t s) {
+  k_lk_pcg_init<<<1, kLkThreads, 0, s>>>(lk, ctl, B);
+  REG_LAUNCH();
+}
+void lk_pcg_check(double* lk, int* ctl, int B, int cap, int maxit, unsigned long long h_if,
+                  unsigned long long h_while, cudaStream_t s) {
+  k_lk_pcg_check<<<1, kLkThreads, 0, s>>>(lk, ctl, B, cap, maxit, (cudaGraphConditionalHandle)h_if,
+                                          (cudaGraphConditionalHandle)h_while);
+  REG_LAUNCH();
+}
+void lk_pcg_alpha(double* lk, int* ctl, int B, cudaStream_t s) {
+  k_lk_pcg_alpha<<<1, kLkThreads, 0, s>>>(lk, ctl, B);
+  REG_LAUNCH();
+}
+void lk_pcg_beta(double* lk, int* ctl, int B, cudaStream_t s) {
+  k_lk_pcg_beta<<<1, kLkThreads, 0, s>>>(lk, ctl, B);
+  REG_LAUNCH();
+}
+void lk_ls_init(double* lk, int* ctl, int B, double hd, cudaStream_t s) {
+  k_lk_ls_init<<<1, kLkThreads, 0, s>>>(lk, ctl, B, hd);
+  REG_LAUNCH();
+}
+void lk_ls_check(double* lk, int* ctl, int B, int max_bt, unsigned long long h_if, unsigned long long h_while,
+                 cudaStream_t s) {
+  k_lk_ls_check<<<1, kLkThreads, 0, s>>>(lk, ctl, B, max_bt, (cudaGraphConditionalHandle)h_if,
+                                         (cudaGraphConditionalHandle)h_while);
+  REG_LAUNCH();
+}
+void lk_ls_armijo(double* lk, int B, double hd, double c1, double rho, cudaStream_t s) {
+  k_lk_ls_armijo<<<1, kLkThreads, 0, s>>>(lk, B, hd, c1, rho);
+  REG_LAUNCH();
+}
+void lk_ls_final(double* lk, int B, int status_ls, cudaStream_t s) {
+  k_lk_ls_final<<<1, kLkThreads, 0, s>>>(lk, B, status_ls);
+  REG_LAUNCH();
+}
+
 void seg_dot(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s, double* out) {
   seg_reduce(RED_DOT, a, b, K, B, N1, scratch, s, out);
 }

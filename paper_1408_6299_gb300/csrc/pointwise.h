@@ -65,5 +65,64 @@ void seg_maxabs(const double* a, int K, int B, long N1, double* scratch, cudaStr
 // out = a_p x + c_p y per problem p; a_dev, c_dev: B coefficients on the device (out may alias y)
 void lincomb_seg(const double* a_dev, const double* x, const double* c_dev, const double* y, double* out, int K,
                  int B, long N1, cudaStream_t s);
+// the same reductions with the B results left in device memory (no synchronisation;
+// usable inside a captured graph)
+void seg_dot_dev(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                 double* out_dev);
+void seg_sqdiff_dev(const double* a, const double* b, int K, int B, long N1, double* scratch, cudaStream_t s,
+                    double* out_dev);
+
+// ---------------------------------------------------------------------------
+// Per-problem scalars of the device-driven lockstep loops (PCG, Nocedal &
+// Wright Alg. 5.3, with the forcing term of Eq. termination-criterion-ksm;
+// Armijo backtracking, Sec. 3.2): rows of B doubles in one array lk, and an
+// int control block ctl. Every decision a problem takes is the host loop's,
+// in the same floating-point operations (no contraction), so a problem follows
+// the same iterates either way.
+// ---------------------------------------------------------------------------
+enum LockSlot {
+  LK_ACT = 0,   // problem still iterating (1/0)
+  LK_ON,        // PCG still running for the problem
+  LK_ETA,       // forcing term
+  LK_G2,        // ||g||_2
+  LK_G02,       // ||g_0||_2
+  LK_RZ, LK_RZN, LK_RN2, LK_PHP,
+  LK_A,         // PCG step length (0 for problems not running)
+  LK_NEGC,      // 1: copy p into s (negative curvature at the first PCG step)
+  LK_KEEP,      // 1 - LK_NEGC
+  LK_MZ, LK_BT, // coefficients of p = mz z + bt p
+  LK_ONE, LK_ZERO, LK_MONE,
+  LK_J,         // objective at the iterate
+  LK_JT,        // trial objective
+  LK_SLOPE,     // <g, s>_h
+  LK_ALPHA,     // line-search step length
+  LK_SRCH,      // line search still running
+  LK_D2, LK_R2, // distance and regularisation sums of the trial point (unscaled)
+  LK_PCG, LK_MV, LK_NPDE, LK_LS,  // counters added to the reports
+  LK_STATUS,    // reg_status set on the device (0: none)
+  LK_COUNT
+};
+enum LockCtl { LC_IT = 0, LC_PIT, LC_LST, LC_ON, LC_COUNT };
+// constants and counters reset; LK_ON = LK_ACT, LK_ETA = min(0.5, sqrt(g2 / g02)); ctl zeroed
+void lk_pcg_init(double* lk, int* ctl, int B, cudaStream_t s);
+// top of a PCG iteration (after rn2 = <r, r>): stop the problems that reached
+// the forcing term; sets the IF handle (some problem runs and fewer than
+// maxit iterations ran in this PCG solve) and the WHILE handle (the same, and
+// fewer than cap iterations ran in this launch)
+void lk_pcg_check(double* lk, int* ctl, int B, int cap, int maxit, unsigned long long h_if,
+                  unsigned long long h_while, cudaStream_t s);
+// after pHp = <p, H p>: step lengths, curvature guard, counters
+void lk_pcg_alpha(double* lk, int* ctl, int B, cudaStream_t s);
+// after rzn = <r, z>: coefficients of the new direction
+void lk_pcg_beta(double* lk, int* ctl, int B, cudaStream_t s);
+// line search: slope *= h_d; alpha = 1 and search for active problems
+void lk_ls_init(double* lk, int* ctl, int B, double hd, cudaStream_t s);
+// top of a trial: IF handle (some problem searches), WHILE handle (and fewer than max_bt trials)
+void lk_ls_check(double* lk, int* ctl, int B, int max_bt, unsigned long long h_if, unsigned long long h_while,
+                 cudaStream_t s);
+// after the trial objective (LK_D2, LK_R2): Armijo test, backtracking
+void lk_ls_armijo(double* lk, int B, double hd, double c1, double rho, cudaStream_t s);
+// problems still searching fail (REG_ELINESEARCH); stopped problems take no step
+void lk_ls_final(double* lk, int B, int status_ls, cudaStream_t s);
 
 }  // namespace reg

@@ -10,6 +10,7 @@
 // (ckpt_every = K). The body-force time integral uses the trapezoid rule on
 // the nodes (default) or the stage values of the discrete adjoint.
 #include <chrono>
+#include <functional>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -161,8 +162,18 @@ struct reg_ctx {
   size_t gsig = 0;
   long gkernels = 0;
   DBuf<double> gdir, gout;
+  // device-driven lockstep loops (stacked problems): per-problem scalars, the
+  // control block, and the graphs of the PCG and line-search loops
+  DBuf<double> lk;
+  DBuf<int> lkc;
+  std::vector<double> lkh;
+  cudaGraphExec_t lk_pcg = nullptr, lk_ls = nullptr;
+  size_t lk_sig = 0;
+  int lk_state = 0;  // 0 not built yet, 1 built, -1 refused (host-driven loops)
   ~reg_ctx() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (lk_pcg) cudaGraphExecDestroy(lk_pcg);
+    if (lk_ls) cudaGraphExecDestroy(lk_ls);
   }
 
   long N() const { return g.N; }
@@ -1533,6 +1544,163 @@ struct LockState {
 // problem S[slot[q]]. Returns true when it stops early so that the caller can
 // restack the remaining problems: at the start of an outer iteration, when at
 // most half of a stack of at least `restack_min` problems is still running.
+// ---------------------------------------------------------------------------
+// Device-driven loops of the lockstep solve. The PCG iteration and the Armijo
+// trial of all problems of a stack run as CUDA graphs with conditional nodes:
+// a WHILE node whose body runs a one-block check kernel (which stops the
+// problems that are done and sets the loop conditions on the device) and an
+// IF node holding one iteration (matvec, per-problem reductions into device
+// rows, step lengths, vector updates). The host launches one graph per loop
+// and reads the per-problem scalars back once per outer iteration. Every loop
+// is bounded: PCG by kLockCap iterations per launch (the host relaunches while
+// problems run and the iteration cap allows), the line search by the number
+// of trials.
+// ---------------------------------------------------------------------------
+constexpr int kLockCap = 256;
+
+// objective parts of stacked problems, unscaled, into device rows
+void objective_seg_dev(reg_ctx* c, const double* v, double* d2_dev, double* r2_dev) {
+  const long N = c->N();
+  const int B = c->g.B;
+  Work<double>& w = c->w64;
+  REG_CUDA(cudaMemcpyAsync(w.m.get(N), c->mT.p, N * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+  state_steps<double>(c, v, 0, c->n_t, nullptr, nullptr, 0, nullptr);
+  double* scr = c->seg_scr.get(seg_scratch_doubles(B));
+  seg_sqdiff_dev(c->mR.p, w.m.p, 1, B, c->g.N1, scr, c->s, d2_dev);
+  double* Rv = c->tmpB.get(c->ncdN());
+  tail(c, v, nullptr, Rv);
+  seg_dot_dev(v, Rv, c->n_c * c->d, B, c->g.N1, scr, c->s, r2_dev);
+}
+
+// A WHILE loop in graph G around [check kernel -> IF(one iteration)].
+void add_bounded_loop(cudaGraph_t G, cudaStream_t s,
+                      const std::function<void(cudaGraphConditionalHandle, cudaGraphConditionalHandle)>& check,
+                      const std::function<void()>& body) {
+  cudaGraphConditionalHandle hw, hi;
+  REG_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  REG_CUDA(cudaGraphAddNode(&wn, G, nullptr, nullptr, 0, &wp));
+  cudaGraph_t wbody = wp.conditional.phGraph_out[0];
+  REG_CUDA(cudaGraphConditionalHandleCreate(&hi, wbody, 0, cudaGraphCondAssignDefault));
+  cudaGraph_t done = nullptr;
+  REG_CUDA(cudaStreamBeginCaptureToGraph(s, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  try {
+    check(hi, hw);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    REG_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in;
+    REG_CUDA(cudaGraphAddNode(&in, cg, deps, nullptr, nd, &ip));
+    REG_CUDA(cudaStreamUpdateCaptureDependencies(s, &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+    REG_CUDA(cudaStreamEndCapture(s, &done));
+    REG_CUDA(cudaStreamBeginCaptureToGraph(s, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    body();
+    REG_CUDA(cudaStreamEndCapture(s, &done));
+  } catch (...) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(s, &done);
+    (void)cudaGetLastError();
+    throw;
+  }
+}
+
+size_t lock_signature(reg_ctx* c, const double* v) {
+  size_t h = graph_signature(c);
+  const void* ptrs[] = {v, c->sv_g.p, c->sv_s.p, c->sv_r.p, c->sv_z.p, c->sv_p.p, c->sv_Hp.p, c->sv_vt.p,
+                        c->lk.p, c->lkc.p, c->seg_scr.p, c->tmpB.p, c->mT.p, c->mR.p};
+  for (const void* p : ptrs) h = (h ^ (size_t)p) * 1099511628211ull;
+  return h;
+}
+
+// Builds (once per stack and buffer set) the PCG and line-search graphs.
+// Returns false when the runtime refuses them (the host-driven loops run).
+bool build_lock_graphs(reg_ctx* c, double* v, const reg_solve_opts& o, long maxit) {
+  const size_t sig = lock_signature(c, v);
+  if (c->lk_state == 1 && sig == c->lk_sig) return true;
+  if (c->lk_state == -1) return false;
+  if (c->lk_pcg) cudaGraphExecDestroy(c->lk_pcg);
+  if (c->lk_ls) cudaGraphExecDestroy(c->lk_ls);
+  c->lk_pcg = c->lk_ls = nullptr;
+  const int B = c->g.B, K = c->n_c * c->d;
+  const long N1 = c->g.N1, n = c->ncdN();
+  double* g = c->sv_g.p;
+  double* sv = c->sv_s.p;
+  double* r = c->sv_r.p;
+  double* z = c->sv_z.p;
+  double* p = c->sv_p.p;
+  double* Hp = c->sv_Hp.p;
+  double* vt = c->sv_vt.p;
+  double* lk = c->lk.p;
+  int* ctl = c->lkc.p;
+  double* scr = c->seg_scr.get(seg_scratch_doubles(B));
+  auto row = [&](int slot) { return lk + (long)slot * B; };
+  const int cap_it = (int)std::min<long>(maxit, 1L << 30);
+  (void)n;
+  cudaGraph_t G1 = nullptr, G2 = nullptr;
+  try {
+    REG_CUDA(cudaGraphCreate(&G1, 0));
+    add_bounded_loop(
+        G1, c->s,
+        [&](cudaGraphConditionalHandle hi, cudaGraphConditionalHandle hw) {
+          lk_pcg_check(lk, ctl, B, kLockCap, cap_it, (unsigned long long)hi, (unsigned long long)hw, c->s);
+        },
+        [&]() {
+          hessvec_body(c, p, Hp);
+          seg_dot_dev(p, Hp, K, B, N1, scr, c->s, row(LK_PHP));
+          lk_pcg_alpha(lk, ctl, B, c->s);
+          lincomb_seg(row(LK_NEGC), p, row(LK_KEEP), sv, sv, K, B, N1, c->s);
+          lincomb_seg(row(LK_A), p, row(LK_ONE), sv, sv, K, B, N1, c->s);
+          lincomb_seg(row(LK_A), Hp, row(LK_ONE), r, r, K, B, N1, c->s);
+          precond(c, r, z);
+          seg_dot_dev(r, z, K, B, N1, scr, c->s, row(LK_RZN));
+          lk_pcg_beta(lk, ctl, B, c->s);
+          lincomb_seg(row(LK_MZ), z, row(LK_BT), p, p, K, B, N1, c->s);
+          seg_dot_dev(r, r, K, B, N1, scr, c->s, row(LK_RN2));
+        });
+    REG_CUDA(cudaGraphInstantiate(&c->lk_pcg, G1, 0));
+    REG_CUDA(cudaGraphCreate(&G2, 0));
+    add_bounded_loop(
+        G2, c->s,
+        [&](cudaGraphConditionalHandle hi, cudaGraphConditionalHandle hw) {
+          lk_ls_check(lk, ctl, B, o.max_backtracks, (unsigned long long)hi, (unsigned long long)hw, c->s);
+        },
+        [&]() {
+          lincomb_seg(row(LK_ONE), v, row(LK_ALPHA), sv, vt, K, B, N1, c->s);
+          objective_seg_dev(c, vt, row(LK_D2), row(LK_R2));
+          lk_ls_armijo(lk, B, c->hd, o.armijo_c1, o.backtrack, c->s);
+        });
+    REG_CUDA(cudaGraphInstantiate(&c->lk_ls, G2, 0));
+  } catch (const CudaError& e) {
+    if (G1) cudaGraphDestroy(G1);
+    if (G2) cudaGraphDestroy(G2);
+    if (c->lk_pcg) cudaGraphExecDestroy(c->lk_pcg);
+    if (c->lk_ls) cudaGraphExecDestroy(c->lk_ls);
+    c->lk_pcg = c->lk_ls = nullptr;
+    (void)cudaGetLastError();
+    c->lk_state = -1;
+    return false;
+  }
+  cudaGraphDestroy(G1);
+  cudaGraphDestroy(G2);
+  c->lk_sig = sig;
+  c->lk_state = 1;
+  return true;
+}
+
 bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S, const std::vector<int>& slot,
                     bool resume, int restack_min) {
   const int B = c->g.B;
@@ -1595,6 +1763,20 @@ bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S
     }
   };
   gradient_seg(c, v, g, dist, regt);
+  // the device-driven loops (Krylov method without CFL halving); one ordinary
+  // matvec first allocates every buffer and settles the autotuned passes
+  bool graph_mode = false;
+  {
+    const char* env = getenv("REG_LOCKSTEP_GRAPHS");
+    if (o.method == REG_METHOD_KRYLOV && !(o.cfl_max > 0) && !(env && env[0] == '0')) {
+      c->lk.get((size_t)LK_COUNT * B);
+      c->lkc.get(LC_COUNT);
+      if (c->lk_state == 0) hessvec_body(c, g, Hp);
+      graph_mode = build_lock_graphs(c, v, o, maxit);
+    }
+    for (int q = 0; q < B; ++q)
+      if (graph_mode) R(q).device_loops = 1;
+  }
   if (!resume) {
     sg.maxabs(g, ginf);
     sg.dot(g, g, tmp);
@@ -1638,7 +1820,56 @@ bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S
     }
     std::vector<double> act(B);
     for (int q = 0; q < B; ++q) act[q] = active[q] ? 1.0 : 0.0;
-    if (o.method == REG_METHOD_PICARD) {
+    std::vector<double> slope, alpha(B, 0.0), Jt(B, 0.0);
+    if (graph_mode) {
+      // PCG and line search of every problem on the device (see build_lock_graphs)
+      const int K = c->n_c * c->d;
+      const long N1 = c->g.N1;
+      double* lk = c->lk.p;
+      int* ctl = c->lkc.p;
+      double* scr = c->seg_scr.get(seg_scratch_doubles(B));
+      auto row = [&](int slot) { return lk + (long)slot * B; };
+      std::vector<double>& h = c->lkh;
+      h.assign((size_t)LK_COUNT * B, 0.0);
+      for (int q = 0; q < B; ++q) {
+        h[(size_t)LK_ACT * B + q] = active[q] ? 1.0 : 0.0;
+        h[(size_t)LK_G2 * B + q] = g2[q];
+        h[(size_t)LK_G02 * B + q] = g02[q];
+        h[(size_t)LK_J * B + q] = J[q];
+      }
+      REG_CUDA(cudaMemcpyAsync(lk, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->s));
+      lk_pcg_init(lk, ctl, B, c->s);
+      REG_CUDA(cudaMemsetAsync(s, 0, n * sizeof(double), c->s));
+      REG_CUDA(cudaMemcpyAsync(r, g, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s));
+      precond(c, r, z);
+      lincomb_seg(row(LK_MONE), z, row(LK_ZERO), z, p, K, B, N1, c->s);
+      seg_dot_dev(r, z, K, B, N1, scr, c->s, row(LK_RZ));
+      seg_dot_dev(r, r, K, B, N1, scr, c->s, row(LK_RN2));
+      for (;;) {  // each launch runs at most kLockCap iterations
+        REG_CUDA(cudaMemsetAsync(ctl + LC_IT, 0, sizeof(int), c->s));
+        REG_CUDA(cudaGraphLaunch(c->lk_pcg, c->s));
+        int hc[LC_COUNT];
+        REG_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, c->s));
+        REG_CUDA(cudaStreamSynchronize(c->s));
+        if (!(hc[LC_ON] && hc[LC_PIT] < maxit && hc[LC_IT] >= kLockCap)) break;
+      }
+      seg_dot_dev(g, s, K, B, N1, scr, c->s, row(LK_SLOPE));
+      lk_ls_init(lk, ctl, B, c->hd, c->s);
+      REG_CUDA(cudaGraphLaunch(c->lk_ls, c->s));
+      lk_ls_final(lk, B, REG_ELINESEARCH, c->s);
+      REG_CUDA(cudaMemcpyAsync(h.data(), lk, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+      REG_CUDA(cudaStreamSynchronize(c->s));
+      for (int q = 0; q < B; ++q) {
+        active[q] = h[(size_t)LK_ACT * B + q] != 0.0;
+        const int st = (int)h[(size_t)LK_STATUS * B + q];
+        if (st) R(q).status = st;
+        R(q).pcg_iters += (long)h[(size_t)LK_PCG * B + q];
+        R(q).matvecs += (long)h[(size_t)LK_MV * B + q];
+        R(q).n_pde += (long)h[(size_t)LK_NPDE * B + q];
+        R(q).ls_trials += (int)h[(size_t)LK_LS * B + q];
+        alpha[q] = h[(size_t)LK_ALPHA * B + q];
+      }
+    } else if (o.method == REG_METHOD_PICARD) {
       precond(c, g, s);
       std::vector<double> sc(B);
       for (int q = 0; q < B; ++q) sc[q] = active[q] ? (o.step_memory ? -amem[q] : -1.0) : 0.0;
@@ -1707,7 +1938,7 @@ bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S
       }
     }
     // keep each step inside the CFL bound by halving it (Sec. 3.3.5)
-    if (o.cfl_max > 0) {
+    if (!graph_mode && o.cfl_max > 0) {
       std::vector<int> halvings(B, 0);
       for (;;) {
         sg.comb(one, v, one, s, vt);
@@ -1732,7 +1963,7 @@ bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S
       }
     }
     // Armijo backtracking from alpha = 1, per problem
-    std::vector<double> slope, alpha(B, 0.0), Jt(B, 0.0);
+    if (!graph_mode) {
     sg.dot(g, s, slope);
     for (double& x : slope) x *= c->hd;
     std::vector<int> searching(B, 0);
@@ -1766,6 +1997,7 @@ bool solve_lockstep(reg_ctx* c, double* v, const reg_solve_opts& o, LockState& S
         R(q).status = REG_ELINESEARCH;
         alpha[q] = 0.0;
       }
+    }
     for (int q = 0; q < B; ++q) {
       if (!active[q]) alpha[q] = 0.0;
       if (active[q] && o.method == REG_METHOD_PICARD && o.step_memory)

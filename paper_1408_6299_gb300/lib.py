@@ -80,6 +80,7 @@ class SolveReport(ctypes.Structure):
         ("J_prev", ctypes.c_double),
         ("dv_inf", ctypes.c_double),
         ("v_inf", ctypes.c_double),
+        ("device_loops", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -94,3 +94,20 @@ def test_lockstep_restacks_running_problems():
         assert abs(r["J"] - r1["J"]) <= 1e-11 * r1["J"] and abs(r["dist_rel"] - r1["dist_rel"]) <= 1e-9
         outers.append(r["outer"])
     assert len(set(outers)) > 1  # the problems stop at different iterations
+
+
+@pytest.mark.parametrize("precision", [lib.REG_FP64, lib.REG_MIXED])
+def test_device_driven_loops_take_the_host_loops_iterates(batch, precision, monkeypatch):
+    # the PCG and line-search loops as conditional CUDA graphs take every
+    # decision the host-driven loops take, problem by problem
+    probs = problems_of(batch)
+    monkeypatch.setenv("REG_LOCKSTEP_GRAPHS", "1")
+    dev = lib.solve_lockstep(probs, precision, grad_rtol=1e-3)
+    monkeypatch.setenv("REG_LOCKSTEP_GRAPHS", "0")
+    probs_h = problems_of(batch)
+    host = lib.solve_lockstep(probs_h, precision, grad_rtol=1e-3)
+    for a, b, qa, qb in zip(dev, host, probs, probs_h):
+        assert a["device_loops"] == 1 and b["device_loops"] == 0
+        for k in ("status", "outer", "pcg_iters", "matvecs", "n_pde", "ls_trials"):
+            assert a[k] == b[k], (k, a[k], b[k])
+        assert rel(qa["v"], qb["v"]) < 1e-12
