@@ -5,6 +5,7 @@
 
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 
 #include "fused.cuh"
@@ -20,19 +21,89 @@ constexpr int row_elems() {
   return sizeof(T) == 4 ? 4096 : 2048;
 }
 
+template <typename T, int L, int NF, bool PROD, int RB>
+void r2c_launch(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out,
+                int zmask, const cx<T>* tw, const cx<T>* twrc) {
+  dim3 grid((unsigned)((g.rows + RB - 1) / RB));
+  k_rows_r2c_n<T, L, RB, NF, PROD><<<grid, kThreads, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
+  REG_LAUNCH();
+}
+
+// Choice of the autotuner among variants 0..nv-1 of a pure pass (one that
+// writes only what it does not read, so running it again gives the same
+// result): the persistent or per-process choice for `key`, else, outside a
+// stream capture, each variant runs three times on the call's own buffers,
+// timed with CUDA events on the stream, after one untimed run of each; the
+// fastest is recorded. During a capture the first variant is used untuned.
+template <typename Run>
+int tuned_choice(const std::string& key, int nv, cudaStream_t st, Run run) {
+  static std::mutex mu;
+  static std::map<std::string, int> mem;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = mem.find(key);
+    if (it != mem.end()) return it->second;
+  }
+  int pick = tune_lookup(key);
+  if (pick < 0 || pick >= nv) {
+    const char* env = getenv("REG_AUTOTUNE");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    REG_CUDA(cudaStreamIsCapturing(st, &cs));
+    if ((env && env[0] == '0') || cs != cudaStreamCaptureStatusNone) return 0;
+    cudaEvent_t e0, e1;
+    REG_CUDA(cudaEventCreate(&e0));
+    REG_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    pick = 0;
+    for (int v = 0; v < nv; ++v) run(v);
+    for (int v = 0; v < nv; ++v) {
+      float total = 0;
+      for (int r = 0; r < 3; ++r) {
+        REG_CUDA(cudaEventRecord(e0, st));
+        run(v);
+        REG_CUDA(cudaEventRecord(e1, st));
+        REG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        REG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        total += ms;
+      }
+      if (total < best) {
+        best = total;
+        pick = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, pick);
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  mem[key] = pick;
+  return pick;
+}
+
 template <typename T, int L, int NF, bool PROD>
 void r2c_L(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out, int zmask,
            const cx<T>* tw, const cx<T>* twrc) {
   constexpr int M = L / 2;
   // single precision, one field: 2048 complex values per block (16 rows at L = 256) measured best
-  // against 1024 and 8192 on the 256^3 matvec
+  // against 1024 and 8192 on the 256^3 matvec; the autotuner also tries half as many rows per block
   constexpr int RB0 = row_elems<T>() / (pow2_ceil(NF) * M * (sizeof(T) == 4 && NF == 1 ? 2 : 1));
   constexpr int RB = RB0 < 1 ? 1 : RB0;
+  constexpr int RBh = RB > 1 ? RB / 2 : 1;
   ProfScope ps(KK_ROWS_R2C, s, (double)g.N * sizeof(T) * (2 * NF + (PROD ? 1 : 0)),
                (double)g.rows * NF * (fft_flops<M>() + 8.0 * M));
-  dim3 grid((unsigned)((g.rows + RB - 1) / RB));
-  k_rows_r2c_n<T, L, RB, NF, PROD><<<grid, kThreads, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
-  REG_LAUNCH();
+  auto run = [&](int v) {
+    if (v == 0) r2c_launch<T, L, NF, PROD, RB>(g, s, in, lam, out, zmask, tw, twrc);
+    else r2c_launch<T, L, NF, PROD, RBh>(g, s, in, lam, out, zmask, tw, twrc);
+  };
+  int v = 0;
+  if (RBh != RB) {
+    const std::string key = tune_device_tag() + "|rows_r2c|" + (sizeof(T) == 4 ? "f32" : "f64") + "|L" +
+                            std::to_string(L) + "|nf" + std::to_string(NF) + (PROD ? "p" : "") + "|rows" +
+                            std::to_string(g.rows);
+    v = tuned_choice(key, 2, s, run);
+  }
+  run(v);
 }
 
 template <typename T, int NF, bool PROD>
@@ -205,7 +276,8 @@ void deriv2_variant(int v, const cx<T>* in, cx<T>* out, const cx<T>* add, long s
   }
 }
 
-// Autotuner of the column derivative pass. Fields larger than 16 MB stream
+// Autotuner of the column derivative pass (choices also persisted, see
+// tune.cu). Fields larger than 16 MB stream
 // through DRAM (the input was written by the previous pass, partly still in
 // L2): there the persistent double-buffered variant is used whenever it is
 // admissible; isolated trials, warm or flushed, do not reproduce that state
@@ -233,9 +305,18 @@ int deriv2_choice(long s, long outer, const cx<T>* tw, cudaStream_t st) {
   auto key = std::make_tuple((int)sizeof(T), L, s, outer);
   auto it = tu.best.find(key);
   if (it != tu.best.end()) return it->second;
-  int pick = -1;
+  const std::string pkey = tune_device_tag() + "|cols|" + (sizeof(T) == 4 ? "f32" : "f64") + "|L" +
+                           std::to_string(L) + "|s" + std::to_string(s) + "|outer" + std::to_string(outer);
+  int pick = tune_lookup(pkey);
+  if (pick >= 0 && pick < 4 && deriv2_variant_ok<T, L>(pick, s, outer)) {
+    tu.best[key] = pick;
+    return pick;
+  }
+  pick = -1;
   const char* env = getenv("REG_AUTOTUNE");
-  bool tune = !(env && env[0] == '0');
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  REG_CUDA(cudaStreamIsCapturing(st, &cs));
+  bool tune = !(env && env[0] == '0') && cs == cudaStreamCaptureStatusNone;  // no trials inside a capture
   const size_t field = (size_t)s * outer * L * sizeof(cx<T>);
   if (field > (16ull << 20) && deriv2_variant_ok<T, L>(0, s, outer)) {
     tu.best[key] = 0;
@@ -284,6 +365,7 @@ int deriv2_choice(long s, long outer, const cx<T>* tw, cudaStream_t st) {
   for (int v = 0; v < 4 && pick < 0; ++v)
     if (deriv2_variant_ok<T, L>(v, s, outer)) pick = v;
   tu.best[key] = pick;
+  if (pick >= 0) tune_store(pkey, pick);
   return pick;
 }
 

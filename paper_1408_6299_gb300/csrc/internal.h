@@ -102,6 +102,12 @@ Grid make_grid(int d, const int64_t* n, int batch = 1);
 // set the text that reg_last_error(NULL) returns on this thread
 void set_thread_error(const std::string& msg);
 
+// Persistent autotuner choices (tune.cu): -1 when the key has none yet.
+// Keys start with tune_device_tag() (device name / multiprocessor count).
+int tune_lookup(const std::string& key);
+void tune_store(const std::string& key, int choice);
+std::string tune_device_tag();
+
 // Batched power-of-two FFTs and Fourier multipliers on one grid, in precision T.
 template <typename T>
 class Spectral {
