@@ -317,8 +317,9 @@ def solve_pairs(pairs, workers, mode="lockstep"):
 
 def batch_sample(count, workers):
     pairs = batch_pairs(count)
-    solve_pairs(pairs[:min(4, count)], workers, "executor")  # warm-up: tuning, tables
-    solve_pairs(pairs[:min(4, count)], workers, "lockstep")
+    # warm-up: the autotuner's trials for every stack size, tables, graph capture
+    solve_pairs(pairs[:min(4, count)], workers, "executor")
+    solve_pairs(pairs, workers, "lockstep")
     tl, reps = solve_pairs(pairs, workers, "lockstep")
     os.environ["REG_LOCKSTEP_GRAPHS"] = "0"  # the same lockstep solve with host-driven loops
     th, _ = solve_pairs(pairs, workers, "lockstep")

@@ -98,9 +98,11 @@ void r2c_L(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam,
   };
   int v = 0;
   if (RBh != RB) {
+    long rb = 1;  // row count rounded up to a power of two: stacks of similar size share a choice
+    while (rb < g.rows) rb *= 2;
     const std::string key = tune_device_tag() + "|rows_r2c|" + (sizeof(T) == 4 ? "f32" : "f64") + "|L" +
                             std::to_string(L) + "|nf" + std::to_string(NF) + (PROD ? "p" : "") + "|rows" +
-                            std::to_string(g.rows);
+                            std::to_string(rb);
     v = tuned_choice(key, 2, s, run);
   }
   run(v);
