@@ -51,19 +51,19 @@ __device__ __forceinline__ void r2c_pack(const cx<T>* buf, long row0, long nrows
   using C = cx<T>;
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
-  constexpr int H = M / 2 + 1;
-  for (int e = threadIdx.x; e < NF * RB * H; e += kThreads) {
-    int seq = e / H, k = e % H;
-    int f = seq / RB, r = seq % RB;
-    long row = row0 + r;
+  // M/2 work items per sequence (a power of two, so the item index splits by
+  // shifts): item k >= 1 writes the modes k and M - k, item 0 the packed
+  // DC/Nyquist slot and the middle mode M/2
+  constexpr int Q2 = M / 2;
+  for (int e = threadIdx.x; e < NF * RB * Q2; e += kThreads) {
+    const int seq = e / Q2, item = e % Q2;
+    const int f = seq / RB, r = seq % RB;
+    const long row = row0 + r;
     if (row >= nrows) continue;
     C* o = out[f] + row * M;
     const C* b = buf + seq * RS;
-    bool dz = (zmask >> f) & 1;
-    if (k == 0) {
-      C z0 = b[0];
-      o[0] = dz ? mk<C>(0, 0) : mk<C>(z0.x + z0.y, z0.x - z0.y);
-    } else {
+    const bool dz = (zmask >> f) & 1;
+    auto pair = [&](int k) {
       C zk = b[pad16(k)], zm = b[pad16(M - k)];
       C E = cscale(cadd(zk, cconj(zm)), (T)0.5);
       C Od = cscale(cmul_mi(csub(zk, cconj(zm))), (T)0.5);
@@ -76,6 +76,13 @@ __device__ __forceinline__ void r2c_pack(const cx<T>* buf, long row0, long nrows
       }
       o[k] = xk;
       if (k != M - k) o[M - k] = xm;
+    };
+    if (item == 0) {
+      C z0 = b[0];
+      o[0] = dz ? mk<C>(0, 0) : mk<C>(z0.x + z0.y, z0.x - z0.y);
+      pair(M / 2);
+    } else {
+      pair(item);
     }
   }
 }
@@ -292,9 +299,10 @@ __device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, l
   return so;
 }
 
-// Inverse row transforms of one staged row block (NF fields x RB rows of
-// packed spectra in buf, padded rows of RS) and the stage epilogue of rows
-// row0..row0+RB-1. Called by all threads of the block after buf is complete.
+// Inverse row transforms of one staged row block (NF fields x RB rows in buf,
+// padded rows of RS, already unpacked from the half spectra and conjugated)
+// and the stage epilogue of rows row0..row0+RB-1. Called by all threads of
+// the block after buf is complete.
 // NE = 1 (advection only): the block then transforms the epilogue's out1
 // values forward in the same buffer and writes their packed spectrum to
 // em.out[0].
@@ -307,24 +315,6 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
   static_assert(NE == 0 || (NE == 1 && EPI == EPI_ADV), "only one-field advection stages emit a spectrum");
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
-  constexpr int H = M / 2 + 1;
-  for (int e = threadIdx.x; e < NF * RB * H; e += kThreads) {
-    int seq = e / H, k = e % H;
-    C* b = buf + seq * RS;
-    if (k == 0) {
-      C p = b[0];
-      b[0] = cconj(mk<C>((p.x + p.y) * (T)0.5, (p.x - p.y) * (T)0.5));
-    } else {
-      C xk = b[pad16(k)], xm = b[pad16(M - k)];
-      C E = cscale(cadd(xk, cconj(xm)), (T)0.5);
-      C Od = cscale(cmul(csub(xk, cconj(xm)), cconj(__ldg(&twrc[k]))), (T)0.5);
-      C zk = mk<C>(E.x - Od.y, E.y + Od.x);
-      C zm = mk<C>(E.x + Od.y, -E.y + Od.x);
-      b[pad16(k)] = cconj(zk);
-      if (k != M - k) b[pad16(M - k)] = cconj(zm);
-    }
-  }
-  __syncthreads();
   smem_fft<T, M, false, kThreads, NF * RB>(buf, RS, tw);
   const T s = (T)1 / (T)M;
   constexpr int ITER = (RB * M + kThreads - 1) / kThreads;
@@ -458,27 +448,39 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NE > 0 ? 5 : 6) : 
   constexpr int NB = NX > NE ? NX : NE;         // sequences the buffer holds
   __shared__ C buf[NB * RB * RS];
   const long row0 = (long)blockIdx.x * RB;
-  constexpr int PER = (NX * RB * M + kThreads - 1) / kThreads;
-  C v[PER];
+  // Prologue: M/2 work items per sequence; item k >= 1 loads the modes k and
+  // M - k of its row, item 0 the packed DC/Nyquist slot and the middle mode
+  // M/2. Each applies the z-derivative (zmask; the DIVS form adds its inputs)
+  // and unpacks the half spectrum for the complex inverse transform in
+  // registers, so buf is filled by one store pass.
+  constexpr int Q2 = M / 2;
+  constexpr int PER = (NX * RB * Q2 + kThreads - 1) / kThreads;
+  C va[PER], vb[PER];
+  auto mode = [&](int f, long row, int k) {
+    C z = mk<C>(0, 0);
+    if constexpr (EPI == EPI_DIVS) {
+#pragma unroll
+      for (int g = 0; g < NF; ++g) {
+        C x = in.p[g][row * M + k];
+        if ((zmask >> g) & 1) x = mk<C>(-(T)k * x.y, (T)k * x.x);
+        z = cadd(z, x);
+      }
+    } else {
+      z = in.p[f][row * M + k];
+      if ((zmask >> f) & 1) z = mk<C>(-(T)k * z.y, (T)k * z.x);
+    }
+    return z;
+  };
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    int e = threadIdx.x + i * kThreads;
-    v[i] = mk<C>(0, 0);
-    if (e < NX * RB * M) {
-      int f = e / (RB * M), rem = e % (RB * M);
-      long row = row0 + rem / M;
+    const int e = threadIdx.x + i * kThreads;
+    va[i] = vb[i] = mk<C>(0, 0);
+    if (e < NX * RB * Q2) {
+      const int seq = e / Q2, item = e % Q2;
+      const long row = row0 + seq % RB;
       if (row < nrows) {
-        if constexpr (EPI == EPI_DIVS) {
-          const int j = rem % M;
-#pragma unroll
-          for (int g = 0; g < NF; ++g) {
-            C z = in.p[g][row * M + j];
-            if ((zmask >> g) & 1) z = mk<C>(-(T)j * z.y, (T)j * z.x);
-            v[i] = cadd(v[i], z);
-          }
-        } else {
-          v[i] = in.p[f][row * M + rem % M];
-        }
+        va[i] = mode(seq / RB, row, item);
+        vb[i] = mode(seq / RB, row, item == 0 ? M / 2 : M - item);
       }
     }
   }
@@ -495,13 +497,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NE > 0 ? 5 : 6) : 
   }
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    int e = threadIdx.x + i * kThreads;
-    if (e < NX * RB * M) {
-      int f = e / (RB * M), rem = e % (RB * M);
-      int j = rem % M;
-      C z = v[i];
-      if (EPI != EPI_DIVS && ((zmask >> f) & 1)) z = mk<C>(-(T)j * z.y, (T)j * z.x);
-      buf[(f * RB + rem / M) * RS + pad16(j)] = z;
+    const int e = threadIdx.x + i * kThreads;
+    if (e < NX * RB * Q2) {
+      const int seq = e / Q2, item = e % Q2;
+      C* b = buf + seq * RS;
+      // modes k and M - k of the half spectrum -> complex sequence values (conjugated:
+      // the inverse runs as a forward FFT)
+      auto unpack = [&](int k, C xk, C xm) {
+        C E = cscale(cadd(xk, cconj(xm)), (T)0.5);
+        C Od = cscale(cmul(csub(xk, cconj(xm)), cconj(__ldg(&twrc[k]))), (T)0.5);
+        C zk = mk<C>(E.x - Od.y, E.y + Od.x);
+        C zm = mk<C>(E.x + Od.y, -E.y + Od.x);
+        b[pad16(k)] = cconj(zk);
+        if (k != M - k) b[pad16(M - k)] = cconj(zm);
+      };
+      if (item == 0) {
+        const C p = va[i];
+        b[0] = cconj(mk<C>((p.x + p.y) * (T)0.5, (p.x - p.y) * (T)0.5));
+        unpack(M / 2, vb[i], vb[i]);
+      } else {
+        unpack(item, va[i], vb[i]);
+      }
     }
   }
   __syncthreads();
