@@ -327,7 +327,16 @@ def batch_sample(count, workers):
     tb, repb = solve_pairs(pairs, workers, "executor")
     ts, _ = solve_pairs(pairs, 1, "executor")
     ok = sum(1 for r in reps if r["status"] == 0 and r["g_inf"] <= 1e-2 * r["g0_inf"])
-    return {"pairs": count, "lockstep_solves_per_s": count / tl,
+    by_shape = {}  # each shape's stack solved alone (lockstep, device-driven loops)
+    for n in sorted({p["n"] for p in pairs}):
+        grp = [p for p in pairs if p["n"] == n]
+        tg, rg = solve_pairs(grp, workers, "lockstep")
+        by_shape["x".join(map(str, n))] = {
+            "pairs": len(grp), "n_t": grp[0]["n_t"], "seconds": tg,
+            "mean_outer": sum(r["outer"] for r in rg) / len(grp),
+            "mean_matvecs": sum(r["matvecs"] for r in rg) / len(grp),
+            "max_matvecs": max(r["matvecs"] for r in rg)}
+    return {"pairs": count, "lockstep_solves_per_s": count / tl, "lockstep_by_shape": by_shape,
             "lockstep_device_loops": sum(r["device_loops"] for r in reps),
             "lockstep_host_loops_solves_per_s": count / th, "executor_solves_per_s": count / tb,
             "executor_workers": workers, "sequential_solves_per_s": count / ts, "speedup_vs_sequential": ts / tl,
@@ -648,6 +657,11 @@ def run_ours(args):
             "clocks": ck, "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "fp64": fp64,
             "store_all": store_all, "newton": newton, "as_configured": as_cfg, "solve_to_rel_grad_1e-2": solves, "batch_2d": batch, "cpu_baseline": cpu,
             "kernel_ms_per_matvec": {k: round(v["ms"], 3) for k, v in prof_all.items()},
+            # every kernel kind of the profiled matvec: algorithmic bytes / event-timed duration
+            "roofline_by_kind": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                                     "GB_per_s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1),
+                                     "frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)}
+                                 for k, v in prof_all.items() if v["ms"] > 0 and v["bytes"] > 0},
         }
         print(json.dumps(line), flush=True)
     R.close()

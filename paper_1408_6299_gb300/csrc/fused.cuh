@@ -299,30 +299,197 @@ __device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, l
   return so;
 }
 
-// Inverse row transforms of one staged row block (NF fields x RB rows in buf,
-// padded rows of RS, already unpacked from the half spectra and conjugated)
-// and the stage epilogue of rows row0..row0+RB-1. Called by all threads of
-// the block after buf is complete.
+// Divergence epilogue on the point pair q with the divergence value k (scaled,
+// real space): Heun stage update and, in stage 1, the optional body-force
+// accumulation (see DivEpi).
+template <typename T>
+__device__ __forceinline__ void div_point(const DivEpi<T>& dv, cx<T> k, long q) {
+  using C = cx<T>;
+  if (dv.src) {
+    C sv = reinterpret_cast<const C*>(dv.src)[q];
+    k = mk<C>(k.x + sv.x, k.y + sv.y);
+  }
+  if (dv.stage == 0) {
+    reinterpret_cast<C*>(dv.out1)[q] = k;
+    return;
+  }
+  C yv = reinterpret_cast<const C*>(dv.y)[q];
+  if (dv.stage != 1) {
+    reinterpret_cast<C*>(dv.out1)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
+    return;
+  }
+  C o1 = mk<C>(yv.x + dv.h * k.x, yv.y + dv.h * k.y);
+  reinterpret_cast<C*>(dv.out1)[q] = o1;
+  reinterpret_cast<C*>(dv.out2)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
+  if (!dv.f_hi) return;
+  // products of the point pair with every component, then per coefficient
+  // all loads before any store
+  C ta[3], tb[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ta[i] = tb[i] = mk<C>(0, 0);
+    if (i < dv.d) {
+      C ga = reinterpret_cast<const C*>(dv.gmA + i * dv.N)[q];
+      ta[i] = mk<C>(yv.x * ga.x, yv.y * ga.y);
+      if (dv.gmC) {
+        C gc = reinterpret_cast<const C*>(dv.gmC + i * dv.N)[q];
+        C yc = reinterpret_cast<const C*>(dv.yC)[q];
+        ta[i] = mk<C>(ta[i].x + yc.x * gc.x, ta[i].y + yc.y * gc.y);
+      }
+      if (dv.gmB) {
+        C gb = reinterpret_cast<const C*>(dv.gmB + i * dv.N)[q];
+        tb[i] = mk<C>(o1.x * gb.x, o1.y * gb.y);
+      }
+    }
+  }
+  for (int l = 0; l < dv.nc; ++l) {
+    C hi[3], lo[3];
+    C* Hf = reinterpret_cast<C*>(dv.f_hi + (long)l * dv.d * dv.N);
+    C* Lo = dv.f_lo ? reinterpret_cast<C*>(dv.f_lo + (long)l * dv.d * dv.N) : nullptr;
+    const long hN = dv.N / 2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < dv.d) {
+        hi[i] = Hf[i * hN + q];
+        lo[i] = Lo ? Lo[i * hN + q] : mk<C>(0, 0);
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (i < dv.d) {
+        T t0 = dv.cA[l] * ta[i].x + dv.cB[l] * tb[i].x;
+        T t1 = dv.cA[l] * ta[i].y + dv.cB[l] * tb[i].y;
+        if (Lo) {
+          C h = hi[i];
+          T s0 = h.x + t0, b0 = s0 - h.x, s1 = h.y + t1, b1 = s1 - h.y;
+          lo[i].x += (h.x - (s0 - b0)) + (t0 - b0);
+          lo[i].y += (h.y - (s1 - b1)) + (t1 - b1);
+          Hf[i * hN + q] = mk<C>(s0, s1);
+          Lo[i * hN + q] = lo[i];
+        } else {
+          Hf[i * hN + q] = mk<C>(hi[i].x + t0, hi[i].y + t1);
+        }
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Edge stage of the two-stage forward row transforms (Plan<M>: M = R0 * R1).
+// The last stage runs in registers and feeds the pack directly: butterfly
+// j < R0 of a sequence yields the modes k = j + R0 r (r < R1). The pack
+// combines mode k with mode M - k, which sits in butterfly (R0 - j) mod R0 at
+// r' = R1 - 1 - r (for j = 0 in the same butterfly at (R1 - r) mod R1). The
+// R0 butterflies of a sequence are neighbouring lanes of one warp, so the
+// partner values arrive by warp shuffles instead of a shared-memory round
+// trip, and each lane packs only its own modes.
+// ---------------------------------------------------------------------------
+template <int M>
+struct Edge {
+  static constexpr int R0 = Plan<M>::R[0], R1 = Plan<M>::R[1];
+  // two stages, at most 8 values per edge butterfly (a lane holds them and
+  // its partner's), whole sequences inside a warp: M = 32, 64, 128
+  static constexpr bool ok = Plan<M>::S == 2 && R1 <= 8 && R0 <= 32 && 32 % R0 == 0;
+};
+
+// p[r] = value of mode M - k for k = j + R0 r, given this lane's x[r] (mode k).
+// Every lane of the warp must call it (full-warp shuffles).
+template <typename T, int R0, int R1>
+__device__ __forceinline__ void edge_partners(const cx<T> (&x)[R1], cx<T> (&p)[R1], int j) {
+  const int lane = threadIdx.x & 31;
+  const int src = lane - j + ((R0 - j) & (R0 - 1));
+#pragma unroll
+  for (int r = 0; r < R1; ++r) {
+    const cx<T> v = x[R1 - 1 - r];
+    const T a = __shfl_sync(0xffffffffu, v.x, src);
+    const T b = __shfl_sync(0xffffffffu, v.y, src);
+    p[r] = j == 0 ? x[(R1 - r) % R1] : mk<cx<T>>(a, b);
+  }
+}
+
+// Forward pack of mode k >= 1 of a real row from the complex FFT values zk =
+// Z[k], zm = Z[M - k] of its M complex pairs: X[k] = E + W^k Od with E =
+// (zk + conj zm)/2, Od = -i (zk - conj zm)/2. dz: times i k (last-axis derivative).
+template <typename T>
+__device__ __forceinline__ cx<T> pack_mode(int k, cx<T> zk, cx<T> zm, const cx<T>* __restrict__ twrc, bool dz) {
+  using C = cx<T>;
+  C E = cscale(cadd(zk, cconj(zm)), (T)0.5);
+  C Od = cscale(cmul_mi(csub(zk, cconj(zm))), (T)0.5);
+  C xk = cadd(E, cmul(__ldg(&twrc[k]), Od));
+  if (dz) xk = mk<C>(-(T)k * xk.y, (T)k * xk.x);
+  return xk;
+}
+// the packed slot 0 (DC + i Nyquist) from Z[0]
+template <typename T>
+__device__ __forceinline__ cx<T> pack_slot0(cx<T> z0, bool dz) {
+  return dz ? mk<cx<T>>(0, 0) : mk<cx<T>>(z0.x + z0.y, z0.x - z0.y);
+}
+// Edge stage of the forward row transforms and the pack: S sequences of RS
+// padded values in buf after the first stage (radix R0, Stockham order);
+// sequence s is field s / RB, row row0 + s % RB, written to out[s / RB].
+// All NT threads call it.
+template <typename T, int M, int RB, int S, int NT>
+__device__ __forceinline__ void edge_forward_pack(const cx<T>* buf, long row0, long nrows, cx<T>* const* out,
+                                                  int zmask, const cx<T>* __restrict__ tw1,
+                                                  const cx<T>* __restrict__ twrc) {
+  constexpr int NO = S / RB;  // output fields
+  using C = cx<T>;
+  constexpr int R0 = Edge<M>::R0, R1 = Edge<M>::R1, RS = padded_len(M);
+  constexpr int TASKS = S * R0;
+  static_assert(NT % 32 == 0, "whole warps");
+#pragma unroll
+  for (int it = 0; it < (TASKS + NT - 1) / NT; ++it) {
+    const int u = threadIdx.x + it * NT;
+    if (u - (int)(threadIdx.x & 31) >= TASKS) break;  // the whole warp is past the end (uniform)
+    const bool act = u < TASKS;
+    const int seq = act ? u / R0 : 0, j = u % R0;
+    const C* b = buf + seq * RS;
+    C x[R1];
+#pragma unroll
+    for (int r = 0; r < R1; ++r) x[r] = b[pad16(j + R0 * r)];
+#pragma unroll
+    for (int r = 1; r < R1; ++r) x[r] = cmul(x[r], __ldg(&tw1[r * R0 + j]));
+    Dft<T, R1>::run(x);
+    C p[R1];
+    edge_partners<T, R0, R1>(x, p, j);
+    const long row = row0 + seq % RB;
+    if (act && row < nrows) {
+      const int f = seq / RB;
+      const bool dz = (zmask >> f) & 1;
+      C* o = out[0];  // the field's pointer by selection (constant indices only)
+#pragma unroll
+      for (int g = 1; g < NO; ++g)
+        if (f == g) o = out[g];
+      o += row * M;
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int k = j + R0 * r;
+        o[k] = (r == 0 && j == 0) ? pack_slot0<T>(x[0], dz) : pack_mode<T>(k, x[r], p[r], twrc, dz);
+      }
+    }
+  }
+}
+
+// Stage epilogue of rows row0..row0+RB-1 from the inverse transforms in buf
+// (NF sequences x RB rows of RS padded values, natural order, conjugated and
+// unscaled), each thread taking the point pairs threadIdx.x + it * NT.
 // NE = 1 (advection only): the block then transforms the epilogue's out1
 // values forward in the same buffer and writes their packed spectrum to
 // em.out[0].
-template <typename T, int L, int RB, int NF, int EPI, int NE>
-__device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
-                                          const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
-                                          const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB,
-                                          const Emit<T>& em) {
+template <typename T, int L, int RB, int NF, int EPI, int NE, int NT>
+__device__ __forceinline__ void c2r_tail(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
+                                         const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
+                                         const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB,
+                                         const Emit<T>& em) {
   using C = cx<T>;
   static_assert(NE == 0 || (NE == 1 && EPI == EPI_ADV), "only one-field advection stages emit a spectrum");
   constexpr int M = L / 2;
   constexpr int RS = padded_len(M);
-  smem_fft<T, M, false, kThreads, NF * RB>(buf, RS, tw);
   const T s = (T)1 / (T)M;
-  constexpr int ITER = (RB * M + kThreads - 1) / kThreads;
+  constexpr int ITER = (RB * M + NT - 1) / NT;
   constexpr int NEA = NE > 0 ? NE : 1;
   C ev[ITER][NEA];  // emitted values (point pairs) of this thread
 #pragma unroll
   for (int it = 0; it < ITER; ++it) {
-    const int e = threadIdx.x + it * kThreads;
+    const int e = threadIdx.x + it * NT;
 #pragma unroll
     for (int f = 0; f < NEA; ++f) ev[it][f] = mk<C>(0, 0);
     if (e >= RB * M) continue;
@@ -342,73 +509,7 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
       const C sa = adv_point<T, NF / 2>(adv, g, q, nullptr);
       adv_point<T, NF / 2>(advB, g + NF / 2, q, advB.src_from_a ? &sa : nullptr);
     } else {
-      C k = g[0];
-      if (dv.src) {
-        C sv = reinterpret_cast<const C*>(dv.src)[q];
-        k = mk<C>(k.x + sv.x, k.y + sv.y);
-      }
-      if (dv.stage == 0) {
-        reinterpret_cast<C*>(dv.out1)[q] = k;
-        continue;
-      }
-      C yv = reinterpret_cast<const C*>(dv.y)[q];
-      if (dv.stage == 1) {
-        C o1 = mk<C>(yv.x + dv.h * k.x, yv.y + dv.h * k.y);
-        reinterpret_cast<C*>(dv.out1)[q] = o1;
-        reinterpret_cast<C*>(dv.out2)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
-        if (dv.f_hi) {
-          // products of the point pair with every component, then per
-          // coefficient all loads before any store
-          C ta[3], tb[3];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            ta[i] = tb[i] = mk<C>(0, 0);
-            if (i < dv.d) {
-              C ga = reinterpret_cast<const C*>(dv.gmA + i * dv.N)[q];
-              ta[i] = mk<C>(yv.x * ga.x, yv.y * ga.y);
-              if (dv.gmC) {
-                C gc = reinterpret_cast<const C*>(dv.gmC + i * dv.N)[q];
-                C yc = reinterpret_cast<const C*>(dv.yC)[q];
-                ta[i] = mk<C>(ta[i].x + yc.x * gc.x, ta[i].y + yc.y * gc.y);
-              }
-              if (dv.gmB) {
-                C gb = reinterpret_cast<const C*>(dv.gmB + i * dv.N)[q];
-                tb[i] = mk<C>(o1.x * gb.x, o1.y * gb.y);
-              }
-            }
-          }
-          for (int l = 0; l < dv.nc; ++l) {
-            C hi[3], lo[3];
-            C* Hf = reinterpret_cast<C*>(dv.f_hi + (long)l * dv.d * dv.N);
-            C* Lo = dv.f_lo ? reinterpret_cast<C*>(dv.f_lo + (long)l * dv.d * dv.N) : nullptr;
-            const long hN = dv.N / 2;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-              if (i < dv.d) {
-                hi[i] = Hf[i * hN + q];
-                lo[i] = Lo ? Lo[i * hN + q] : mk<C>(0, 0);
-              }
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-              if (i < dv.d) {
-                T t0 = dv.cA[l] * ta[i].x + dv.cB[l] * tb[i].x;
-                T t1 = dv.cA[l] * ta[i].y + dv.cB[l] * tb[i].y;
-                if (Lo) {
-                  C h = hi[i];
-                  T s0 = h.x + t0, b0 = s0 - h.x, s1 = h.y + t1, b1 = s1 - h.y;
-                  lo[i].x += (h.x - (s0 - b0)) + (t0 - b0);
-                  lo[i].y += (h.y - (s1 - b1)) + (t1 - b1);
-                  Hf[i * hN + q] = mk<C>(s0, s1);
-                  Lo[i * hN + q] = lo[i];
-                } else {
-                  Hf[i * hN + q] = mk<C>(hi[i].x + t0, hi[i].y + t1);
-                }
-              }
-          }
-        }
-      } else {
-        reinterpret_cast<C*>(dv.out1)[q] = mk<C>(yv.x + (T)0.5 * dv.h * k.x, yv.y + (T)0.5 * dv.h * k.y);
-      }
+      div_point<T>(dv, g[0], q);
     }
   }
   if constexpr (NE > 0) {
@@ -416,16 +517,28 @@ __device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, con
     __syncthreads();  // every thread has read the inverse transforms from buf
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
-      const int e = threadIdx.x + it * kThreads;
+      const int e = threadIdx.x + it * NT;
       if (e < RB * M) {
 #pragma unroll
         for (int f = 0; f < NE; ++f) buf[(f * RB + e / M) * RS + pad16(e % M)] = ev[it][f];
       }
     }
     __syncthreads();
-    smem_fft<T, M, false, kThreads, NE * RB>(buf, RS, tw);
+    smem_fft<T, M, false, NT, NE * RB>(buf, RS, tw);
     r2c_pack<T, L, RB, NE>(buf, row0, nrows, em.out, 0, twrc);
   }
+}
+
+// Inverse row transforms of one staged row block (NF fields x RB rows in buf,
+// padded rows of RS, already unpacked from the half spectra and conjugated),
+// then the stage epilogue. Called by all threads of the block after buf is complete.
+template <typename T, int L, int RB, int NF, int EPI, int NE>
+__device__ __forceinline__ void c2r_block(cx<T>* buf, long row0, long nrows, const AdvEpi<T>& adv,
+                                          const DivEpi<T>& dv, const cx<T>* __restrict__ tw,
+                                          const cx<T>* __restrict__ twrc, const AdvEpi<T>& advB,
+                                          const Emit<T>& em) {
+  smem_fft<T, L / 2, false, kThreads, NF * RB>(buf, padded_len(L / 2), tw);
+  c2r_tail<T, L, RB, NF, EPI, NE, kThreads>(buf, row0, nrows, adv, dv, tw, twrc, advB, em);
 }
 
 
@@ -522,6 +635,60 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (NE > 0 ? 5 : 6) : 
   }
   __syncthreads();
   c2r_block<T, L, RB, NX, EPI, NE>(buf, row0, nrows, adv, dv, tw, twrc, advB, em);
+}
+
+// ---------------------------------------------------------------------------
+// Real-to-complex row pass on the edge-stage transforms (Edge<M>::ok): the
+// first stage (radix R0) straight from global memory, then the edge stage
+// plus pack in registers, so the block's values cross shared memory once.
+// The complex-to-real counterpart is k_rows_c2r_p (after the copy helpers).
+// ---------------------------------------------------------------------------
+template <typename T, int L, int RB, int NF, bool PROD, int NT>
+__global__ void __launch_bounds__(NT) k_rows_r2c_e(RowsIn<T, NF> in, const T* __restrict__ lam,
+                                                    RowsOut<T, NF> out, int zmask, long nrows,
+                                                    const cx<T>* __restrict__ tw, const cx<T>* __restrict__ twrc) {
+  using C = cx<T>;
+  constexpr int M = L / 2, R0 = Edge<M>::R0, R1 = Edge<M>::R1, RS = padded_len(M);
+  static_assert(Edge<M>::ok, "edge-stage plan");
+  __shared__ C buf[NF * RB * RS];
+  const long row0 = (long)blockIdx.x * RB;
+  // first stage: butterfly j < R1 of a sequence takes the complex pairs j + R1 r (r < R0)
+  constexpr int T0 = NF * RB * R1;
+#pragma unroll
+  for (int it = 0; it < (T0 + NT - 1) / NT; ++it) {
+    const int u = threadIdx.x + it * NT;
+    if (u < T0) {
+      const int seq = u / R1, j = u % R1;
+      const long row = row0 + seq % RB;
+      C v[R0];
+      if (row < nrows) {
+        const long q = row * M + j;
+        const T* src = in.p[0];
+#pragma unroll
+        for (int g = 1; g < NF; ++g)
+          if (seq / RB == g) src = in.p[g];
+        const C* x = reinterpret_cast<const C*>(src) + q;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          C z = x[r * R1];
+          if (PROD) {
+            const C l = reinterpret_cast<const C*>(lam)[q + r * R1];
+            z = mk<C>(z.x * l.x, z.y * l.y);
+          }
+          v[r] = z;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R0; ++r) v[r] = mk<C>(0, 0);
+      }
+      Dft<T, R0>::run(v);
+      C* b = buf + seq * RS;
+#pragma unroll
+      for (int r = 0; r < R0; ++r) b[pad16(j * R0 + r)] = v[r];
+    }
+  }
+  __syncthreads();
+  edge_forward_pack<T, M, RB, NF * RB, NT>(buf, row0, nrows, out.p, zmask, tw + stage_tw_offset(M, 1), twrc);
 }
 
 // Spectral derivative along a strided axis of length L on z-spectral rows:

@@ -21,10 +21,44 @@ constexpr int row_elems() {
   return sizeof(T) == 4 ? 4096 : 2048;
 }
 
+// Real-to-complex row passes on the edge-stage transforms (two-stage plans,
+// last axis 64, 128 or 256) unless REG_EDGE_ROWS=0.
+inline bool edge_rows_enabled() {
+  static const bool on = [] {
+    const char* env = getenv("REG_EDGE_ROWS");
+    return !(env && env[0] == '0');
+  }();
+  return on;
+}
+// blocks of kernel `kern` (nt threads, smem dynamic bytes) resident on the
+// whole current device at once
+template <typename K>
+int persistent_wave(K kern, int nt, size_t smem) {
+  REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, dev = 0, sms = 0;
+  REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
+  REG_CUDA(cudaGetDevice(&dev));
+  REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  return (per_sm < 1 ? 1 : per_sm) * sms;
+}
+
+// threads of an edge real-to-complex block: one first-stage butterfly each
+template <int M, int NF, int RB>
+constexpr int edge_r2c_threads() {
+  return (NF * RB * Edge<M>::R1 + 31) / 32 * 32;
+}
 template <typename T, int L, int NF, bool PROD, int RB>
 void r2c_launch(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out,
                 int zmask, const cx<T>* tw, const cx<T>* twrc) {
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
+  if constexpr (Edge<L / 2>::ok) {
+    if (edge_rows_enabled()) {
+      constexpr int NT = edge_r2c_threads<L / 2, NF, RB>();
+      k_rows_r2c_e<T, L, RB, NF, PROD, NT><<<grid, NT, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
+      REG_LAUNCH();
+      return;
+    }
+  }
   k_rows_r2c_n<T, L, RB, NF, PROD><<<grid, kThreads, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
   REG_LAUNCH();
 }
@@ -206,17 +240,6 @@ bool cols_tensor_map(CUtensorMap* m, const cx<T>* in, long s, long outer) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// blocks of kernel `kern` (nt threads, smem dynamic bytes) resident on the
-// whole current device at once
-template <typename K>
-int persistent_wave(K kern, int nt, size_t smem) {
-  REG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0, dev = 0, sms = 0;
-  REG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));
-  REG_CUDA(cudaGetDevice(&dev));
-  REG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  return (per_sm < 1 ? 1 : per_sm) * sms;
-}
 
 // variant 0: persistent double-buffered, tile width TCmax (tiles by TMA where
 // a tensor map can describe them, else by cp.async); variants 1..3:

@@ -274,10 +274,11 @@ def test_transport_adjoint_checkpointed(ckpt_cases, ckpt, quad):
 
 def white_case(n):
     r = np.random.default_rng(404 + sum(n))
+    n_t = max(4, max(n) // 16)  # CFL <= 0.25 for the speed 0.1 below
     if len(n) == 2:
-        c = dict(n=n, n_t=4, n_c=1, beta=1e-2, reg=2, stokes=False)
+        c = dict(n=n, n_t=n_t, n_c=1, beta=1e-2, reg=2, stokes=False)
     else:
-        c = dict(n=n, n_t=4, n_c=2, beta=1e-2, reg=1, stokes=True)
+        c = dict(n=n, n_t=n_t, n_c=2, beta=1e-2, reg=1, stokes=True)
     c["mT"] = synth.white_noise(n, r)
     c["v_true"] = synth.white_noise_velocity(n, r, c["n_c"], 0.1)
     c["vt"] = synth.white_noise_velocity(n, r, c["n_c"], 1.0)
@@ -286,7 +287,14 @@ def white_case(n):
     return c, P
 
 
-@pytest.mark.parametrize("n", [(16, 16), (8, 16, 32)], ids=["16x16", "8x16x32"])
+# Last axes of 64, 128 and 256 points run the edge-stage row kernels (pack and
+# unpack partners over warp shuffles): every butterfly's partner modes and the
+# packed DC/Nyquist slot carry content here, and 8 rows per field leave the
+# divergence pass's row blocks (32 rows in single precision) partly empty.
+FULL_SPECTRUM_SHAPES = [(16, 16), (8, 16, 32), (8, 64), (8, 256), (8, 8, 128), (8, 8, 256)]
+
+
+@pytest.mark.parametrize("n", FULL_SPECTRUM_SHAPES, ids=["x".join(map(str, n)) for n in FULL_SPECTRUM_SHAPES])
 @pytest.mark.parametrize("precision,ckpt", [(lib.REG_FP64, 0), (lib.REG_MIXED, 0), (lib.REG_MIXED, 2)])
 def test_full_spectrum_inputs(n, precision, ckpt):
     c, P = white_case(n)
