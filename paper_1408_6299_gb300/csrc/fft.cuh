@@ -58,14 +58,29 @@ template <typename T, int R, int k> __device__ __forceinline__ cx<T> twid_const(
   else return cmul(o, root16<T, q>());
 }
 
+// e + t and e - t of one radix-2 butterfly. Single precision issues each as
+// one paired instruction (sm_100 and later; e - t as e + (-1) t, exact),
+// the same roundings as the componentwise form. Twiddles that are multiples
+// of -i (a swap and a sign) keep the componentwise form, where the sign
+// folds into the addition.
+template <typename T, int q>
+__device__ __forceinline__ void bfly(cx<T> e, cx<T> t, cx<T>& a, cx<T>& b) {
+  if constexpr (sizeof(T) == 4 && (q == 0 || q % 4 != 0)) {
+    a = __fadd2_rn(e, t);
+    b = __ffma2_rn(t, make_float2(-1.f, -1.f), e);
+  } else {
+    a = cadd(e, t);
+    b = csub(e, t);
+  }
+}
+
 // In-register forward DFT of size R (power of two, R <= 16): radix-2
 // decimation in time, recursively.
 template <typename T, int R> struct Dft {
   template <int k> static __device__ __forceinline__ void comb(cx<T>* v, const cx<T>* e, const cx<T>* o) {
     if constexpr (k < R / 2) {
       cx<T> t = twid_const<T, R, k>(o[k]);
-      v[k] = cadd(e[k], t);
-      v[k + R / 2] = csub(e[k], t);
+      bfly<T, (k * 16 / R) % 16>(e[k], t, v[k], v[k + R / 2]);
       comb<k + 1>(v, e, o);
     }
   }

@@ -147,6 +147,7 @@ struct AdvEpi {
   T h;
   int stage;
   int src_from_a;  // two-field stage, second field: the source is the first field's Sout value
+  int a_from_a;    // two-field stage, second field: same velocity as the first (reuse its loaded values)
   int out1_spectral_only;  // out1 is only passed on as a spectrum (the row pass emits it): no real store
 };
 
@@ -241,9 +242,12 @@ __device__ __forceinline__ void prefetch_epilogue(const AdvEpi<T>& adv, const Di
 // Advection epilogue on the point pair q with the gradient components g[0..D)
 // (-a.g [- source], Heun update, optional keep of g or of g.sw). srcv, when
 // given, is the source value instead of e.src. Returns the Sout value.
+// av_in: the velocity values at q (null: load them); av_out: receives the
+// loaded velocity values when the Heun update ran.
 template <typename T, int D>
 __device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, long q, const cx<T>* srcv,
-                                           cx<T>* o1 = nullptr) {
+                                           cx<T>* o1 = nullptr, const cx<T>* av_in = nullptr,
+                                           cx<T>* av_out = nullptr) {
   using C = cx<T>;
   C so = mk<C>(0, 0);
   if (e.G[0]) {
@@ -265,7 +269,8 @@ __device__ __forceinline__ cx<T> adv_point(const AdvEpi<T>& e, const cx<T>* g, l
   T k0 = 0, k1 = 0;
 #pragma unroll
   for (int f = 0; f < D; ++f) {
-    C a = reinterpret_cast<const C*>(e.a[f])[q];
+    C a = av_in ? av_in[f] : reinterpret_cast<const C*>(e.a[f])[q];
+    if (av_out) av_out[f] = a;
     k0 -= a.x * g[f].x;
     k1 -= a.y * g[f].y;
   }
@@ -506,8 +511,10 @@ __device__ __forceinline__ void c2r_tail(cx<T>* buf, long row0, long nrows, cons
     if (EPI == EPI_ADV) {
       adv_point<T, NF>(adv, g, q, nullptr, &ev[it][0]);
     } else if (EPI == EPI_ADV2) {
-      const C sa = adv_point<T, NF / 2>(adv, g, q, nullptr);
-      adv_point<T, NF / 2>(advB, g + NF / 2, q, advB.src_from_a ? &sa : nullptr);
+      C av[NF / 2 > 0 ? NF / 2 : 1];
+      const C sa = adv_point<T, NF / 2>(adv, g, q, nullptr, nullptr, nullptr, av);
+      adv_point<T, NF / 2>(advB, g + NF / 2, q, advB.src_from_a ? &sa : nullptr, nullptr,
+                           advB.a_from_a ? av : nullptr);
     } else {
       div_point<T>(dv, g[0], q);
     }
@@ -524,8 +531,13 @@ __device__ __forceinline__ void c2r_tail(cx<T>* buf, long row0, long nrows, cons
       }
     }
     __syncthreads();
-    smem_fft<T, M, false, NT, NE * RB>(buf, RS, tw);
-    r2c_pack<T, L, RB, NE>(buf, row0, nrows, em.out, 0, twrc);
+    if constexpr (Edge<M>::ok) {
+      stockham_stage<T, M, Edge<M>::R0, 1, false, NT, NE * RB>(buf, RS, tw);
+      edge_forward_pack<T, M, RB, NE * RB, NT>(buf, row0, nrows, em.out, 0, tw + stage_tw_offset(M, 1), twrc);
+    } else {
+      smem_fft<T, M, false, NT, NE * RB>(buf, RS, tw);
+      r2c_pack<T, L, RB, NE>(buf, row0, nrows, em.out, 0, twrc);
+    }
   }
 }
 

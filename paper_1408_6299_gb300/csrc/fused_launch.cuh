@@ -610,9 +610,11 @@ void adv2_stage_impl(Spectral<T>& sp, const T* uA, const AdvEpi<T>& eA, const T*
   DivEpi<T> none{};
   RowsSpec<T, 6> in6{{XA, YA, UA, XB, YB, UB}};
   // a velocity read by both epilogues (the same node, or n_c = 1) is counted once
-  const bool shared_a = eA.out1 && eB.out1 && eA.a[0] == eB.a[0];
+  const bool shared_a = eA.out1 && eB.out1 && eA.a[0] == eB.a[0] && eA.a[1] == eB.a[1] && eA.a[2] == eB.a[2];
   const double bytes = epi_bytes(eA) + epi_bytes(eB) - (shared_a ? 3.0 * g.N * sizeof(T) : 0.0);
-  c2r<T, 6, EPI_ADV2>(g, s, in6, (1 << 2) | (1 << 5), eA, none, bytes, tw, twrc, eB);
+  AdvEpi<T> eB2 = eB;  // the second epilogue takes the first one's velocity values
+  eB2.a_from_a = shared_a ? 1 : 0;
+  c2r<T, 6, EPI_ADV2>(g, s, in6, (1 << 2) | (1 << 5), eA, none, bytes, tw, twrc, eB2);
 }
 
 template <typename T>
