@@ -531,7 +531,7 @@ __device__ __forceinline__ void c2r_tail(cx<T>* buf, long row0, long nrows, cons
       }
     }
     __syncthreads();
-    if constexpr (Edge<M>::ok) {
+    if constexpr (sizeof(T) == 4 && Edge<M>::ok) {
       stockham_stage<T, M, Edge<M>::R0, 1, false, NT, NE * RB>(buf, RS, tw);
       edge_forward_pack<T, M, RB, NE * RB, NT>(buf, row0, nrows, em.out, 0, tw + stage_tw_offset(M, 1), twrc);
     } else {

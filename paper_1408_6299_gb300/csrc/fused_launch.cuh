@@ -21,8 +21,8 @@ constexpr int row_elems() {
   return sizeof(T) == 4 ? 4096 : 2048;
 }
 
-// Real-to-complex row passes on the edge-stage transforms (two-stage plans,
-// last axis 64, 128 or 256) unless REG_EDGE_ROWS=0.
+// Single-precision real-to-complex row passes on the edge-stage transforms
+// (two-stage plans, last axis 64, 128 or 256) unless REG_EDGE_ROWS=0.
 inline bool edge_rows_enabled() {
   static const bool on = [] {
     const char* env = getenv("REG_EDGE_ROWS");
@@ -51,7 +51,7 @@ template <typename T, int L, int NF, bool PROD, int RB>
 void r2c_launch(const Grid& g, cudaStream_t s, const RowsIn<T, NF>& in, const T* lam, const RowsOut<T, NF>& out,
                 int zmask, const cx<T>* tw, const cx<T>* twrc) {
   dim3 grid((unsigned)((g.rows + RB - 1) / RB));
-  if constexpr (Edge<L / 2>::ok) {
+  if constexpr (sizeof(T) == 4 && Edge<L / 2>::ok) {  // double precision: FP64-pipe-bound, staged kernel
     if (edge_rows_enabled()) {
       constexpr int NT = edge_r2c_threads<L / 2, NF, RB>();
       k_rows_r2c_e<T, L, RB, NF, PROD, NT><<<grid, NT, 0, s>>>(in, lam, out, zmask, g.rows, tw, twrc);
