@@ -1164,6 +1164,7 @@ struct ColJobs {
   long s[kColJobs];             // stride between pencil elements (complex values)
   int ntx[kColJobs];            // tiles across the inner extent s / 16
   int start[kColJobs + 1];      // first global tile of each job; start[nj] = all tiles
+  int rev[kColJobs];            // walk the job's tiles from the last one
   int nj;
 };
 
@@ -1196,9 +1197,13 @@ __global__ void __launch_bounds__(8 * (L / R0 > R0 ? L / R0 : R0)) k_cols_pairs(
       if (k < J.nj && tt >= J.start[k]) q = k;
     return q;
   };
+  auto local = [&](int tt, int q) {  // the job's own tile index of global tile tt
+    const int lt = tt - J.start[q];
+    return J.rev[q] ? J.start[q + 1] - J.start[q] - 1 - lt : lt;
+  };
   auto issue = [&](int tt, int b) {  // one thread
     const int q = job_of(tt);
-    const int lt = tt - J.start[q];
+    const int lt = local(tt, q);
     const CUtensorMap* mp = q == 0 ? &m0 : (q == 1 ? &m1 : (q == 2 ? &m2 : &m3));
     mbar_expect_tx(&bar[b], TILE_BYTES);
     tma_load_2d(bufs + b * L * TC, mp, (lt % J.ntx[q]) * XW, (lt / J.ntx[q]) * L, &bar[b]);
@@ -1221,7 +1226,7 @@ __global__ void __launch_bounds__(8 * (L / R0 > R0 ? L / R0 : R0)) k_cols_pairs(
     float2* pre = cur;               // plane of real parts
     float2* pim = cur + L * TC / 2;  // plane of imaginary parts
     const int q = job_of(t);
-    const int lt = t - J.start[q];
+    const int lt = local(t, q);
     const long s = J.s[q];
     const long off = (long)(lt / J.ntx[q]) * L * s + (long)(lt % J.ntx[q]) * TC;
     const int tn = t + gridDim.x;

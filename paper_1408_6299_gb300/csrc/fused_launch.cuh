@@ -443,6 +443,7 @@ struct ColJob {
   const cx<T>* in;
   cx<T>* out;
   const cx<T>* add;
+  int rev = 0;  // walk the tiles from the last one
 };
 
 template <int L>
@@ -462,6 +463,7 @@ void cols_pairs_L(const Spectral<float>& sp, const Grid& g, const ColJob<float>*
       throw StatusError{3, "column pass: tensor map rejected"};
     J.out[q] = jobs[q].out;
     J.add[q] = jobs[q].add;
+    J.rev[q] = jobs[q].rev;
     J.s[q] = s;
     J.ntx[q] = (int)(s / 16);
     J.start[q] = acc;
@@ -501,7 +503,23 @@ bool cols_pairs(const Spectral<T>& sp, const ColJob<T>* jobs, int nj, cudaStream
           !sp.pair_twiddles(L))
         return false;
     }
-    // one launch per distinct axis length, jobs in their given order
+    // The axis-1 passes run first and walk their tiles from the last one: their
+    // last tiles (largest outer index) read the rows the preceding row pass
+    // wrote last, still in L2. Measured on the 256^3 matvec: 224.8 -> 222.3 ms
+    // against the given order; reversing the axis-0 passes as well changed nothing.
+    ColJob<T> ord[kColJobs];
+    {
+      int m = 0;
+      for (int q = 0; q < nj; ++q)
+        if (jobs[q].axis == 1) {
+          ord[m] = jobs[q];
+          ord[m++].rev = 1;
+        }
+      for (int q = 0; q < nj; ++q)
+        if (jobs[q].axis != 1) ord[m++] = jobs[q];
+      jobs = ord;
+    }
+    // one launch per distinct axis length, jobs in that order
     for (int done = 0; done < nj;) {
       const int L = g.n[jobs[done].axis];
       ColJob<float> grp[kColJobs];
