@@ -165,9 +165,10 @@ void c2r_L(const Grid& g, cudaStream_t s, const RowsSpec<T, NF>& in, int zmask, 
   // single precision: 512 complex values per field and block for one field,
   // 1024 for more (4 and 8 rows at L = 256), so that the epilogue operand
   // slices stay within the prefetch limit (measured on the 256^3 matvec:
-  // 298 -> 290 ms against the element-count rule of the other passes)
+  // 298 -> 290 ms against the element-count rule of the other passes); the
+  // emitting pass (NE = 1) takes 4 rows at L = 256 (222.5 -> 220.4 ms against 8)
   constexpr int NX = EPI == EPI_DIVS ? 1 : NF;  // sequences transformed per row
-  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NX == 1 || NX > 4 ? 8 : 4) * M)
+  constexpr int RB0 = sizeof(T) == 4 ? row_elems<T>() / ((NX == 1 || NX > 4 || NE > 0 ? 8 : 4) * M)
                                      : row_elems<T>() / ((NX > 4 ? 8 : pow2_ceil(NX)) * M);
   constexpr int RB = RB0 < 1 ? 1 : RB0;
   ProfScope ps(KK_ROWS_C2R, s, bytes, (double)g.rows * (NX + NE) * (fft_flops<M>() + 8.0 * M));
